@@ -1,0 +1,420 @@
+#!/usr/bin/env python
+"""Benchmark of the Lidar surface-segmentation path on GB300.
+
+Workload (per rank): 512 seeded ray-cast scans with rings drawn from
+{16, 32, 64, 128} and widths from {1024, 1800, 2048, 4096} (about 69 M points,
+1.1 GB of x,y,z,r input), sub-sampling 1, angle threshold 10 deg.  One step is
+one batched pass over the whole batch (a CUDA-graph replay of the four
+kernels) with inputs resident in HBM.  Inputs are larger than L2, so no flush
+is needed between steps.
+
+The JSON line reports points/s of the batched path (value), the same metric
+end to end through the C ABI with host buffers (e2e: host->device copy of the
+inputs, the pass, device->host copy of labels and segment counts), the plain
+per-scan path (one lsg_segment call per scan), the dominant kernel's HBM
+roofline fraction, and the FP64 oracle timed on the host cores on a bounded
+sample (cpu_baseline).
+
+Multi-GPU: scans are independent, so N ranks each segment their own batch
+(weak scaling, no collective on the data path); timing is the max over ranks.
+
+``--impl reference`` times the FP64 oracle on the host cores instead (the
+reference arm: bounded samples of the same workload, same metric).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "points/sec segmented + p50/p99 scan latency, batched/served vs plain GPU"
+UNIT = "points/s"
+WORKLOAD = ("batch512: 512 seeded ray-cast Lidar scans per GPU, rings {16,32,64,128} x columns "
+            "{1024,1800,2048,4096}, x,y,z,r float32 input, s=1, angle 10 deg, one CUDA-graph pass per step")
+FALLBACK_HBM_GBS = 6800.0
+# algorithmic bytes at s = 1: the pass reads x,y,z,r (16 B) per point and
+# writes labels (4 B) per point plus a mesh byte and a normal (13 B) per
+# vertex, and reads the range once more for validity (4 B): 8 + 25/s
+PATH_BYTES_PER_POINT = 33.0
+# the fused tile kernel alone: 16 B read, 13 B written per point (s = 1)
+TILE_BYTES_PER_POINT = 29.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["lsg", "reference"], default="lsg")
+    ap.add_argument("--scans", type=int, default=512)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.2)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for k, nm in enumerate(names):
+                    if f[5 + k].lower().startswith("active"):
+                        reasons.add(nm)
+            os.unlink(self.path)
+        except Exception:
+            return None
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------------
+# helpers
+# --------------------------------------------------------------------------
+def measured_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def profiled_traffic():
+    """DRAM bytes per point of the tile kernel from the committed ncu summary,
+    valid only while the kernel source is unchanged since the capture."""
+    src = os.path.join(ROOT, "paper_2005_02704_gb300", "csrc", "lsg_kernels.cu")
+    prof = os.path.join(ROOT, "profiles", "k_tile_batch512.md")
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        vals = {}
+        for line in open(prof):
+            if ":" in line and line.strip().startswith("- "):
+                k, v = line.strip()[2:].split(":", 1)
+                vals[k.strip()] = v.strip().strip("`")
+        if vals.get("kernel_source_sha256") != sha:
+            return None
+        return float(vals["dram_bytes_per_point"])
+    except Exception:
+        return None
+
+
+def batch_data(n, rank):
+    import lidarsim
+    specs = lidarsim.batch_specs(n, seed0=2000 + rank * n)
+    scans = [lidarsim.make_scan(sp) for sp in specs]
+    return specs, scans
+
+
+def seg_params(spec):
+    from paper_2005_02704_gb300 import lsg
+    return lsg.Params(subsample=spec.subsample, r_max=spec.r_max, jump_rel_h=spec.jump_rel_h,
+                      jump_rel_v=spec.jump_rel_v, angle_rad=math.radians(spec.angle_deg))
+
+
+def oracle_rate(specs, scans, budget_points, threads):
+    """FP64 oracle over a bounded sample of the batch on the host cores."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle as O
+    stride = max(1, int(math.ceil(sum(s.points for s in scans) / budget_points)))
+    idx = list(range(0, len(scans), stride))
+    pts = sum(scans[i].points for i in idx)
+
+    def one(i):
+        sp = specs[i]
+        p = O.Params(subsample=sp.subsample, r_max=sp.r_max, jump_rel_h=sp.jump_rel_h, jump_rel_v=sp.jump_rel_v,
+                     angle_rad=math.radians(sp.angle_deg))
+        O.segment_scan(scans[i], p)
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(threads) as ex:
+        list(ex.map(one, idx))
+    dt = time.perf_counter() - t0
+    return pts / dt, pts, len(idx), dt
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# --------------------------------------------------------------------------
+# reference arm: the FP64 oracle on the host cores
+# --------------------------------------------------------------------------
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    specs, scans = batch_data(args.scans, 0)
+    cores = host_cores()
+    budget = 4.0e6  # points per step: a bounded sample, a few seconds of host work
+    for _ in range(args.warmup):
+        oracle_rate(specs, scans, budget, cores)
+    rates, pts_total, t_total = [], 0, 0.0
+    for _ in range(args.steps):
+        r, pts, ns, dt = oracle_rate(specs, scans, budget, cores)
+        rates.append(r)
+        pts_total += pts
+        t_total += dt
+    value = pts_total / t_total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t_total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "scans": args.scans},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"every {max(1, int(math.ceil(sum(s.points for s in scans) / budget)))}th "
+                                       f"scan of the batch per step (~{budget / 1e6:.0f} M points)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    from paper_2005_02704_gb300 import batch, lsg
+    lsg.load()
+    specs, scans = batch_data(args.scans, rank)
+    shapes = [batch.ScanShape(s.rings, s.cols, sp.subsample) for sp, s in zip(specs, scans)]
+    db = batch.DeviceBatch(shapes, [seg_params(sp) for sp in specs], local)
+    for b, s in enumerate(scans):
+        db.set_scan(b, s)
+    db.upload()
+    torch.cuda.synchronize()
+    ctx = lsg.Context(local)
+    plan = db.plan(ctx)
+    stream = torch.cuda.current_stream()
+    tuned = None
+    if not args.no_autotune:
+        tuned = plan.autotune(reps=3)
+    tile_name = {v: k for k, v in lsg.TILES.items()}[plan.tile]
+
+    # ---- batched path, inputs resident ------------------------------------
+    for _ in range(max(args.warmup, 3)):
+        plan.run()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier()
+    ms_step = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+    if ctx.error() != lsg.LSG_OK:
+        raise RuntimeError("device error during the timed region")
+    pts_all = sum_over_ranks(float(db.points))
+    value = pts_all / (ms_step / 1e3)
+
+    # ---- per-phase device times (events recorded inside the graph) ---------
+    phase = [0.0, 0.0, 0.0, 0.0]
+    nrep = max(3, min(args.steps, 10))
+    for _ in range(nrep):
+        plan.run()
+        t = plan.phase_times()
+        phase = [a + b for a, b in zip(phase, t)]
+    phase = [x / nrep for x in phase]
+
+    # ---- end to end through the C ABI with host buffers --------------------
+    for _ in range(max(args.warmup, 3)):
+        db.upload()
+        plan.run()
+        db.download()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    h2d = d2h = 0
+    for _ in range(args.steps):
+        h2d = db.upload()
+        plan.run()
+        d2h = db.download()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_e2e = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+    e2e_value = pts_all / (ms_e2e / 1e3)
+
+    # ---- plain per-scan path: one lsg_segment call per scan ----------------
+    plain = None
+    if not args.no_plain:
+        views = [(db.scan_inputs(b), db.view(b)) for b in range(db.n)]
+        outs = [lsg.Outputs(*v) for _, v in views]
+        prm = db.params
+
+        def plain_pass():
+            for b in range(db.n):
+                (elev, xyzr), _ = views[b]
+                ctx.segment(elev, xyzr=xyzr, az0=float(db.az0[b]), daz=float(db.daz[b]), params=prm[b],
+                            out=outs[b], stream=stream)
+
+        for _ in range(2):
+            plain_pass()
+        torch.cuda.synchronize()
+        barrier()
+        npl = max(2, min(args.steps, 5))
+        e0.record(stream)
+        for _ in range(npl):
+            plain_pass()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_plain = max_over_ranks(e0.elapsed_time(e1) / npl)
+        plain = {"value": pts_all / (ms_plain / 1e3), "unit": UNIT, "ms_per_pass": ms_plain,
+                 "scans_per_s": db.n * world / (ms_plain / 1e3),
+                 "gpu_launches_per_pass": 4 * db.n}
+
+    # ---- roofline of the dominant kernel ---------------------------------
+    peak, peak_kind = measured_hbm()
+    t_tile = phase[1] / 1e3
+    achieved = TILE_BYTES_PER_POINT * db.points / t_tile / 1e9
+    traffic_pp = profiled_traffic()
+    roof = {"bound": "hbm", "kernel": "k_tile (decode+mesh+normals+edge mask+tile components)",
+            "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "peak_source": f"{peak_kind} HBM copy bandwidth",
+            "algorithmic_bytes_per_launch": TILE_BYTES_PER_POINT * db.points,
+            "traffic": (traffic_pp * db.points) if traffic_pp is not None else None}
+    path_achieved = PATH_BYTES_PER_POINT * db.points / (ms_step / 1e3) / 1e9
+
+    # ---- CPU baseline: the oracle on the host cores ------------------------
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        cores = host_cores()
+        r, pts, ns, dt = oracle_rate(specs, scans, 25e6, cores)
+        cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{ns} of the 512 scans (every {math.ceil(len(scans) / ns)}th), {pts / 1e6:.1f} M points, "
+                         f"{dt:.1f} s wall on {cores} threads"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "scans_per_gpu": db.n, "points_per_gpu": db.points,
+                       "tile": tile_name, "autotune_ms": tuned[1] if tuned else None,
+                       "l2": "inputs larger than L2 (x,y,z,r %.2f GB per GPU > 129 MB), no flush" % (
+                           db.points * 16 / 1e9),
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roof,
+            "path_roofline": {"bound": "hbm", "achieved": path_achieved, "peak": peak, "unit": "GB/s",
+                              "frac": path_achieved / peak, "bytes_per_point": PATH_BYTES_PER_POINT},
+            "kernel_ms": {"ring_order": phase[0], "tile": phase[1], "merge": phase[2], "labels": phase[3]},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": ms_e2e},
+            "plain": plain,
+            "scans_per_s": db.n * world / (ms_step / 1e3),
+            "gpu_launches": 4 * args.steps,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,250 @@
+/*
+ * lsg.h - C ABI of the GB300 Lidar surface-segmentation library (liblsg.so).
+ *
+ * The library implements the data-parallel path of Mukherjee, Das, Ghosh,
+ * Chowdhury and Saha, "Fast Geometric Surface based Segmentation of Point
+ * Cloud from Lidar Data" (PReMI 2019): one spinning-Lidar scan, organised as
+ * rings x shots, goes in; the mesh, the per-vertex normals and the segment
+ * label of every point come out.  Every step runs in CUDA kernels for sm_103a.
+ *
+ * Conventions shared by all calls
+ * --------------------------------
+ * - Pointers documented as "device" must point to memory of the context's
+ *   device.  The caller allocates and owns every input and output buffer;
+ *   the library owns only its workspace (inside the context or the plan).
+ * - Calls are asynchronous and ordered on the given stream (a cudaStream_t
+ *   passed as void*, NULL = the legacy default stream).  Outputs are valid
+ *   once that stream has synchronised.  Argument and shape errors are
+ *   returned synchronously and launch nothing.  Errors detected on the device
+ *   (a NaN elevation, a bounded wait that ran out) are recorded in a sticky
+ *   error word of the context, read by lsg_get_error.
+ * - A context must not be used from two host threads, or on two streams, at
+ *   the same time: its workspace is shared by its calls.
+ * - Nothing throws across this ABI.
+ *
+ * Grid convention (Sec. 2, mesh construction): ring i counts from the
+ * topmost sensor down (rings are sorted by elevation, descending, ties by
+ * input row); column c counts shots from the first of the spin; with
+ * sub-sampling s the mesh vertices are the columns c = j*s, j < Ws =
+ * ceil(W/s).  All outputs are indexed in this sorted ring order.
+ */
+#ifndef LSG_H
+#define LSG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lsg_ctx lsg_ctx;
+typedef struct lsg_plan lsg_plan;
+typedef void* lsg_stream; /* cudaStream_t */
+
+typedef enum {
+  LSG_OK = 0,
+  LSG_E_ARG = 1,     /* bad pointer or parameter value */
+  LSG_E_SHAPE = 2,   /* negative or too large rings / columns */
+  LSG_E_OOM = 3,     /* device allocation failed */
+  LSG_E_BUDGET = 4,  /* workspace would exceed the context's memory budget */
+  LSG_E_CUDA = 5,    /* a CUDA runtime call failed */
+  LSG_E_TIMEOUT = 6, /* a bounded device-side wait ran out */
+  LSG_E_DEVICE = 7   /* the device flagged bad input data (e.g. NaN elevation) */
+} lsg_status;
+
+/* Homogeneity predicate (Algorithm 1). */
+enum {
+  LSG_PRED_ANGLE = 0,    /* angle(n_p, n_q) < angle_rad */
+  LSG_PRED_COMPONENT = 1 /* |dx| < comp[0], |dy| < comp[1], |dz| < comp[2] */
+};
+
+/* Bits of the per-vertex mesh byte (output meshbits). */
+#define LSG_BIT_R 0x01     /* mesh edge (i,j)-(i,j+1)   (column wraps)   */
+#define LSG_BIT_D 0x02     /* mesh edge (i,j)-(i+1,j)                    */
+#define LSG_BIT_G 0x04     /* mesh edge (i,j)-(i+1,j+1) (column wraps)   */
+#define LSG_BIT_HR 0x08    /* edge R is homogeneous                      */
+#define LSG_BIT_HD 0x10    /* edge D is homogeneous                      */
+#define LSG_BIT_HG 0x20    /* edge G is homogeneous                      */
+#define LSG_BIT_VALID 0x40 /* the vertex is a point of the scan (in range) */
+#define LSG_BIT_HASN 0x80  /* the vertex has a normal                    */
+
+/* Upper limits of one scan. */
+#define LSG_MAX_RINGS 4096
+#define LSG_MAX_COLS (1 << 20)
+#define LSG_MAX_POINTS (1 << 28)
+
+/*
+ * One scan.  Sec. 2: P = {p(theta, phi, r)}, theta the fixed elevation of a
+ * sensor, phi the azimuth of the shot, r the measured range.
+ *   rings, cols     H >= 0 sensors, W >= 0 shots per revolution.
+ *   elevation       device float[H], radians, any order (the library sorts).
+ *   azimuth0, azimuth_step
+ *                   phi_c = azimuth0 + c * azimuth_step (radians; the sign of
+ *                   the step is the spin direction).
+ *   xyzr            device float[H][W][4] = x, y, z, range per shot, rows in
+ *                   the order of `elevation`; 16-byte aligned.  Or NULL:
+ *   range           device float[H][W] ranges; x, y, z are then decoded as
+ *                   r (cos theta cos phi, cos theta sin phi, sin theta).
+ * A range r is a point of the scan when r_min < r <= r_max (r = 0 marks a
+ * dropout).
+ */
+typedef struct {
+  int32_t rings;
+  int32_t cols;
+  const float* elevation;
+  float azimuth0;
+  float azimuth_step;
+  const float* xyzr;
+  const float* range;
+} lsg_scan;
+
+/*
+ * Parameters (lsg_default_params fills the defaults given in brackets).
+ *   subsample   s >= 1, keep every s-th shot as a mesh vertex [1] (Sec. 2).
+ *   r_min, r_max  validity window, 0 <= r_min < r_max [0, 100].
+ *   jump_rel_h, jump_rel_v  depth-jump cut: a mesh edge (p,q) is dropped when
+ *               |r_p - r_q| > tau * min(r_p, r_q), tau = jump_rel_h for the
+ *               R edge and jump_rel_v for D and G [0.10, 1.0]; +inf disables.
+ *               Evaluated in IEEE binary32 round-to-nearest.
+ *   predicate   LSG_PRED_ANGLE or LSG_PRED_COMPONENT [ANGLE].
+ *   angle_rad   angle threshold in (0, pi) [10 deg].
+ *   comp        (I, J, K) > 0 of the component predicate [0.2, 0.2, 0.2]
+ *               (the paper's setting, Sec. 3).
+ *   wrap        1 = join the last column to the first (full 360 deg spin,
+ *               Sec. 2), 0 = open sweep [1].  Wrapping needs Ws >= 3 and is
+ *               ignored below that.
+ */
+typedef struct {
+  int32_t subsample;
+  float r_min;
+  float r_max;
+  float jump_rel_h;
+  float jump_rel_v;
+  int32_t predicate;
+  float angle_rad;
+  float comp[3];
+  int32_t wrap;
+} lsg_params;
+
+/*
+ * Outputs of one scan (device, caller-owned; every pointer required).
+ *   meshbits  uint8[H][Ws]   mesh and homogeneity bits (LSG_BIT_*)
+ *   normals   float[H][Ws][3] unit normal facing the sensor (0 if none):
+ *             n = -sign(azimuth_step) * sum_k w_k V_k x V_k+1 / |...|, over
+ *             the incident triangles (p, q_k, q_k+1) whose three edges are in
+ *             the mesh, spokes V_k = q_k - p in the order (i+1,j), (i+1,j+1),
+ *             (i,j+1), (i-1,j), (i-1,j-1), (i,j-1), w_k = 1/(|V_k|+|V_k+1|)
+ *             (Sec. 2, normal estimation).
+ *   labels    int32[H][W]    segment label of every point: the smallest
+ *             i*W + c over the points of its segment; -1 for points out of
+ *             range.  Non-sampled points take the label of the nearer
+ *             bracketing sampled column on their ring (ties to the earlier,
+ *             falling back to the other when the nearer is unlabelled)
+ *             (Sec. 2, last paragraph; Algorithm 1).
+ *   nseg      int32[1]       number of segments.
+ */
+typedef struct {
+  uint8_t* meshbits;
+  float* normals;
+  int32_t* labels;
+  int32_t* nseg;
+} lsg_out;
+
+/* Tile shapes of the fused kernels (rows x columns of mesh vertices). */
+enum {
+  LSG_TILE_AUTO = -1,
+  LSG_TILE_8x128 = 0,
+  LSG_TILE_4x256 = 1,
+  LSG_TILE_16x64 = 2,
+  LSG_TILE_2x512 = 3,
+  LSG_TILE_8x64 = 4,
+  LSG_TILE_COUNT = 5
+};
+
+/* Fills *p with the defaults listed above. */
+void lsg_default_params(lsg_params* p);
+
+/* Human-readable name of a status code (static string). */
+const char* lsg_status_str(lsg_status s);
+
+/* Creates a context on CUDA device `device` whose workspace may use at most
+ * mem_budget_bytes of device memory (0 = no limit).  *out receives the
+ * context; destroy it with lsg_destroy. */
+lsg_status lsg_create(int device, size_t mem_budget_bytes, lsg_ctx** out);
+
+/* Frees the context and its workspace (synchronises the device first). */
+lsg_status lsg_destroy(lsg_ctx* ctx);
+
+/* Selects the tile shape used by lsg_segment (LSG_TILE_*; AUTO = default). */
+lsg_status lsg_set_tile(lsg_ctx* ctx, int tile);
+
+/*
+ * Segments one scan (Sec. 2: meshing, normal estimation, Algorithm 1,
+ * back-fill): decode -> mesh -> normals -> edge mask -> connected components
+ * -> back-fill.  The workspace (ring order, union-find parents: 4*(2H + H*Ws)
+ * bytes) is allocated in the context on first need.
+ */
+lsg_status lsg_segment(lsg_ctx* ctx, const lsg_scan* scan, const lsg_params* params,
+                       const lsg_out* out, lsg_stream stream);
+
+/*
+ * Labels from a given mesh byte array (the edge mask is taken as given):
+ * the components and back-fill steps of lsg_segment alone (Algorithm 1 and
+ * Sec. 2, last paragraph).  Used to check labelling exactly against another
+ * implementation's mask.
+ *   H, W, s, wrap  grid as in lsg_segment (wrap needs Ws >= 3).
+ *   meshbits       device uint8[H][Ws], sorted ring order; only the
+ *                  homogeneity bits and the valid bit are read.
+ *   valid          device uint8[H][W] (1 = point in range), sorted ring
+ *                  order; may be NULL when s == 1.
+ *   labels, nseg   device outputs as in lsg_out.
+ */
+lsg_status lsg_label_from_mask(lsg_ctx* ctx, int32_t H, int32_t W, int32_t s, int32_t wrap,
+                               const uint8_t* meshbits, const uint8_t* valid, int32_t* labels,
+                               int32_t* nseg, lsg_stream stream);
+
+/*
+ * Batched path: many scans of uneven shape in one pass.  The plan fixes the
+ * scans' device pointers, shapes and parameters, allocates the workspace for
+ * all of them (within the context's budget) and captures the pass in a CUDA
+ * graph; lsg_batch_run replays it.  Rewrite the inputs in place between
+ * replays to process new data of the same shapes.
+ *   n          number of scans (>= 1)
+ *   scans[n], params[n], outs[n]  as for lsg_segment (host arrays, copied)
+ *   tile       LSG_TILE_* shape, or LSG_TILE_AUTO to let lsg_autotune pick
+ *              later (the default shape is used until then).
+ */
+lsg_status lsg_batch_plan(lsg_ctx* ctx, int32_t n, const lsg_scan* scans, const lsg_params* params,
+                          const lsg_out* outs, int tile, lsg_plan** plan);
+
+/* Replays the plan's graph on `stream`. */
+lsg_status lsg_batch_run(lsg_plan* plan, lsg_stream stream);
+
+/* Times every tile shape on the plan (reps replays each, CUDA events on
+ * `stream`), keeps the fastest and re-captures the graph.  *best_tile and
+ * *best_ms (either may be NULL) receive the choice and its time per pass. */
+lsg_status lsg_autotune(lsg_plan* plan, int reps, lsg_stream stream, int* best_tile, float* best_ms);
+
+/* Tile shape the plan currently uses. */
+int lsg_plan_tile(const lsg_plan* plan);
+
+/* Device time of each phase of the plan's last replay, in milliseconds:
+ * ms[0] ring order, ms[1] fused tile kernel (decode, mesh, normals, edge
+ * mask, tile-local components), ms[2] border merge, ms[3] labels and
+ * back-fill.  Measured by CUDA events recorded inside the graph; waits for
+ * the replay to finish. */
+lsg_status lsg_plan_phase_times(lsg_plan* plan, float* ms);
+
+/* Frees the plan (synchronises the device first). */
+lsg_status lsg_plan_destroy(lsg_plan* plan);
+
+/* Reads and clears the context's sticky device error word (synchronises the
+ * device).  LSG_OK when no device-side error was recorded. */
+lsg_status lsg_get_error(lsg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LSG_H */

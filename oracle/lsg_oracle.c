@@ -246,9 +246,11 @@ int oracle_neighbours(int H, int W, int s, int wrap, const unsigned char* mb, in
  * edges exist; w_k = 1 / (|V_k| + |V_k+1|), V_k = q_k - p.
  * normal[3v] = unit normal or 0; bit 7 of mb set when it exists.
  * kappa[v] (optional) = sum_k w_k |V_k| |V_k+1| / |sum_k w_k V_k x V_k+1|,
- * the condition number of the weighted sum (used by the tolerance tests). */
+ * the condition number of the weighted sum; snorm[v] (optional) =
+ * |sum_k w_k V_k x V_k+1|; ntri[v] (optional) = number of counted triangles.
+ * These three only serve the tolerance tests. */
 int oracle_normals(int H, int W, int s, int wrap, float daz, const double* xyz, unsigned char* mb,
-                   double* normal, double* kappa) {
+                   double* normal, double* kappa, double* snorm, int32_t* ntri_out) {
   int Ws = (W + s - 1) / s;
   int wr = o_wrap_eff(wrap, Ws);
   double sgn = daz < 0.0f ? -1.0 : 1.0;
@@ -258,6 +260,8 @@ int oracle_normals(int H, int W, int s, int wrap, float daz, const double* xyz, 
       size_t p = (size_t)i * W + (size_t)j * s;
       normal[3 * v] = normal[3 * v + 1] = normal[3 * v + 2] = 0.0;
       if (kappa) kappa[v] = INFINITY;
+      if (snorm) snorm[v] = 0.0;
+      if (ntri_out) ntri_out[v] = 0;
       mb[v] &= (unsigned char)~OB_HASN;
       if (!(mb[v] & OB_VALID)) continue;
       int sp[6][2];
@@ -286,8 +290,10 @@ int oracle_normals(int H, int W, int s, int wrap, float daz, const double* xyz, 
         mag += w * la * lb;
         ++ntri;
       }
+      if (ntri_out) ntri_out[v] = ntri;
       if (ntri == 0) continue;
       double len = sqrt(sum[0] * sum[0] + sum[1] * sum[1] + sum[2] * sum[2]);
+      if (snorm) snorm[v] = len;
       if (!(len > 0.0)) continue;
       for (int t = 0; t < 3; ++t) normal[3 * v + t] = -sgn * sum[t] / len;
       if (kappa) kappa[v] = mag / len;
@@ -487,13 +493,14 @@ int oracle_backfill(int H, int W, int s, int wrap, const unsigned char* valid,
 
 /* One scan through every step.  Outputs (caller-allocated):
  *   order[H], mb[H*Ws], normal[3*H*Ws] (double), labels[H*W], *nseg;
- *   optional: kappa[H*Ws], margin[3*H*Ws], vlabel[H*Ws].
+ *   optional: kappa[H*Ws], margin[3*H*Ws], vlabel[H*Ws], snorm[H*Ws], ntri[H*Ws].
  * Returns 0, or a negative code on bad input. */
 int oracle_segment(int H, int W, const float* elev, float az0, float daz, const float* xyzr,
                    const float* range, int s, float r_min, float r_max, float jump_h, float jump_v,
                    int pred, double angle_t, const double* comp, int wrap, int* order,
                    unsigned char* mb, double* normal, int32_t* labels, int32_t* nseg,
-                   double* kappa, double* margin, int32_t* vlabel_out) {
+                   double* kappa, double* margin, int32_t* vlabel_out, double* snorm,
+                   int32_t* ntri) {
   if (H < 0 || W < 0 || s < 1) return -1;
   if (H == 0 || W == 0) { *nseg = 0; return 0; }
   int Ws = (W + s - 1) / s;
@@ -507,7 +514,7 @@ int oracle_segment(int H, int W, const float* elev, float az0, float daz, const 
   if (oracle_ring_order(H, elev, order)) { rc = -3; goto done; }
   oracle_decode(H, W, order, elev, az0, daz, xyzr, range, r_min, r_max, rs, xyz, valid);
   oracle_mesh(H, W, s, wrap, rs, valid, jump_h, jump_v, mb);
-  oracle_normals(H, W, s, wrap, daz, xyz, mb, normal, kappa);
+  oracle_normals(H, W, s, wrap, daz, xyz, mb, normal, kappa, snorm, ntri);
   oracle_edge_mask(H, W, s, wrap, pred, angle_t, comp, normal, mb, margin);
   *nseg = oracle_components(H, W, s, wrap, mb, vlabel);
   oracle_backfill(H, W, s, wrap, valid, vlabel, labels);

@@ -56,13 +56,13 @@ def _load():
             "oracle_decode": [I, I, _P, _P, F, F, _P, _P, F, F, _P, _P, _P],
             "oracle_mesh": [I, I, I, I, _P, _P, F, F, _P],
             "oracle_neighbours": [I, I, I, I, _P, _P, _P],
-            "oracle_normals": [I, I, I, I, F, _P, _P, _P, _P],
+            "oracle_normals": [I, I, I, I, F, _P, _P, _P, _P, _P, _P],
             "oracle_edge_mask": [I, I, I, I, I, D, _P, _P, _P, _P],
             "oracle_components": [I, I, I, I, _P, _P],
             "oracle_algorithm1": [I, I, I, I, _P, _P],
             "oracle_backfill": [I, I, I, I, _P, _P, _P],
             "oracle_segment": [I, I, _P, F, F, _P, _P, I, F, F, F, F, I, D, _P, I, _P, _P, _P, _P, _P,
-                               _P, _P, _P],
+                               _P, _P, _P, _P, _P],
             "oracle_label_from_mask": [I, I, I, I, _P, _P, _P, _P],
         }
         for name, args in sig.items():
@@ -107,6 +107,8 @@ class Result:
     kappa: np.ndarray      # float64 [H, Ws]
     margin: np.ndarray     # float64 [H, Ws, 3]
     vlabel: np.ndarray     # int32 [H, Ws]
+    snorm: np.ndarray      # float64 [H, Ws]  |sum_k w_k V_k x V_k+1|
+    ntri: np.ndarray       # int32 [H, Ws]    counted triangles
 
 
 def ws_of(W: int, s: int) -> int:
@@ -143,16 +145,18 @@ def segment(elev, az0: float, daz: float, xyzr: Optional[np.ndarray], p: Params,
     kappa = np.zeros((H, Ws), dtype=np.float64)
     margin = np.zeros((H, Ws, 3), dtype=np.float64)
     vlabel = np.full((H, Ws), -1, dtype=np.int32)
+    snorm = np.zeros((H, Ws), dtype=np.float64)
+    ntri = np.zeros((H, Ws), dtype=np.int32)
     nseg = np.zeros(1, dtype=np.int32)
     comp = _c(p.comp, np.float64)
     rc = lib.oracle_segment(H, W, _ptr(e), float(az0), float(daz), _ptr(xyzr), _ptr(range_), s,
                             float(p.r_min), float(p.r_max), float(p.jump_rel_h), float(p.jump_rel_v),
                             int(p.predicate), float(p.angle_rad), _ptr(comp), int(p.wrap), _ptr(order),
                             _ptr(mb), _ptr(nrm), _ptr(labels), _ptr(nseg), _ptr(kappa), _ptr(margin),
-                            _ptr(vlabel))
+                            _ptr(vlabel), _ptr(snorm), _ptr(ntri))
     if rc != 0:
         raise ValueError(f"oracle_segment failed: {rc}")
-    return Result(order, mb, nrm, labels, int(nseg[0]), kappa, margin, vlabel)
+    return Result(order, mb, nrm, labels, int(nseg[0]), kappa, margin, vlabel, snorm, ntri)
 
 
 def segment_scan(scan, p: Params, range_only: bool = False) -> Result:
@@ -207,7 +211,7 @@ def normals(xyz, mb, W, s, wrap, daz):
     H, Ws = mb.shape
     nrm = np.zeros((H, Ws, 3), np.float64)
     kappa = np.zeros((H, Ws), np.float64)
-    lib.oracle_normals(H, W, s, wrap, float(daz), _ptr(xyz), _ptr(mb), _ptr(nrm), _ptr(kappa))
+    lib.oracle_normals(H, W, s, wrap, float(daz), _ptr(xyz), _ptr(mb), _ptr(nrm), _ptr(kappa), None, None)
     return mb, nrm, kappa
 
 

@@ -1,0 +1,526 @@
+// lsg_api.cu - the C ABI declared in include/lsg.h: contexts, argument
+// checks, workspace, the single-scan and batched passes, graph capture and
+// the tile-shape autotuner.  Host code only; the kernels are in lsg_kernels.cu.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "lsg_internal.h"
+
+using namespace lsg;
+
+struct lsg_ctx {
+  int device = 0;
+  size_t budget = 0;        // 0 = unlimited
+  size_t used = 0;          // bytes currently held (context workspace + plans)
+  void* ws = nullptr;       // single-scan workspace
+  size_t ws_bytes = 0;
+  int32_t* d_err = nullptr; // sticky device error word
+  int tile = LSG_TILE_8x128;
+};
+
+struct lsg_plan {
+  lsg_ctx* ctx = nullptr;
+  int tile = LSG_TILE_8x128;
+  int n = 0;
+  std::vector<ScanDesc> host_desc;  // tile fields filled per tile shape
+  ScanDesc* d_desc = nullptr;
+  int32_t* d_tile_scan = nullptr;
+  int32_t ntiles = 0;
+  void* ws = nullptr;               // order + trig + parent of every scan
+  size_t bytes = 0;                 // everything this plan holds
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // phase boundaries
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+lsg_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return LSG_OK;
+  if (e == cudaErrorMemoryAllocation) return LSG_E_OOM;
+  return LSG_E_CUDA;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Validates one scan's shape and parameters; fills Ws.
+lsg_status check_scan(const lsg_scan* sc, const lsg_params* p, const lsg_out* o, int* Ws_out) {
+  if (!sc || !p || !o) return LSG_E_ARG;
+  if (sc->rings < 0 || sc->cols < 0) return LSG_E_SHAPE;
+  if (sc->rings > LSG_MAX_RINGS || sc->cols > LSG_MAX_COLS) return LSG_E_SHAPE;
+  if ((int64_t)sc->rings * sc->cols > (int64_t)LSG_MAX_POINTS) return LSG_E_SHAPE;
+  if (p->subsample < 1) return LSG_E_ARG;
+  if (!(p->r_min >= 0.f) || !(p->r_max > p->r_min)) return LSG_E_ARG;
+  if (!(p->jump_rel_h >= 0.f) || !(p->jump_rel_v >= 0.f)) return LSG_E_ARG;
+  if (p->predicate == LSG_PRED_ANGLE) {
+    if (!(p->angle_rad > 0.f) || !(p->angle_rad < 3.14159265f)) return LSG_E_ARG;
+  } else if (p->predicate == LSG_PRED_COMPONENT) {
+    for (int k = 0; k < 3; ++k)
+      if (!(p->comp[k] > 0.f)) return LSG_E_ARG;
+  } else {
+    return LSG_E_ARG;
+  }
+  if (!isfinite(sc->azimuth0) || !isfinite(sc->azimuth_step)) return LSG_E_ARG;
+  const int Ws = sc->cols > 0 ? (sc->cols + p->subsample - 1) / p->subsample : 0;
+  *Ws_out = Ws;
+  if (sc->rings == 0 || sc->cols == 0) {
+    if (!o->nseg) return LSG_E_ARG;
+    return LSG_OK;
+  }
+  if (!sc->elevation) return LSG_E_ARG;
+  if (!sc->xyzr && !sc->range) return LSG_E_ARG;
+  if (sc->xyzr && ((uintptr_t)sc->xyzr & 15u)) return LSG_E_ARG;
+  if (!o->meshbits || !o->normals || !o->labels || !o->nseg) return LSG_E_ARG;
+  return LSG_OK;
+}
+
+// Fills the shape/parameter fields of a descriptor (pointers to the
+// workspace are set by the caller).
+ScanDesc make_desc(const lsg_scan* sc, const lsg_params* p, const lsg_out* o, int Ws) {
+  ScanDesc d;
+  memset(&d, 0, sizeof(d));
+  d.xyzr = reinterpret_cast<const float4*>(sc->xyzr);
+  d.range = sc->range;
+  d.elev = sc->elevation;
+  d.valid = nullptr;
+  d.mb = o->meshbits;
+  d.nrm = o->normals;
+  d.labels = o->labels;
+  d.nseg = o->nseg;
+  d.H = sc->rings;
+  d.W = sc->cols;
+  d.Ws = Ws;
+  d.s = p->subsample;
+  d.wrap = (p->wrap && Ws >= 3) ? 1 : 0;
+  d.az0 = sc->azimuth0;
+  d.daz = sc->azimuth_step;
+  d.r_min = p->r_min;
+  d.r_max = p->r_max;
+  d.jump_h = p->jump_rel_h;
+  d.jump_v = p->jump_rel_v;
+  d.pred = p->predicate;
+  d.cos_t = (float)cos((double)p->angle_rad);
+  d.comp_x = p->comp[0];
+  d.comp_y = p->comp[1];
+  d.comp_z = p->comp[2];
+  d.nsign = sc->azimuth_step < 0.f ? 1.f : -1.f;
+  return d;
+}
+
+void set_tiles(ScanDesc& d, int tile, int tile0) {
+  const TileShape ts = tile_shape(tile);
+  d.tiles_r = (d.H + ts.rows - 1) / ts.rows;
+  d.tiles_c = (d.Ws + ts.cols - 1) / ts.cols;
+  d.tile0 = tile0;
+}
+
+size_t scan_ws_bytes(int H, int Ws) {
+  return align_up(sizeof(int32_t) * H, 256) + align_up(sizeof(float2) * H, 256) +
+         align_up(sizeof(int32_t) * (size_t)H * Ws, 256);
+}
+
+void carve_ws(ScanDesc& d, char* base) {
+  d.order = reinterpret_cast<int32_t*>(base);
+  base += align_up(sizeof(int32_t) * d.H, 256);
+  d.trig = reinterpret_cast<float2*>(base);
+  base += align_up(sizeof(float2) * d.H, 256);
+  d.parent = reinterpret_cast<int32_t*>(base);
+}
+
+lsg_status reserve(lsg_ctx* ctx, size_t need) {
+  if (need <= ctx->ws_bytes) return LSG_OK;
+  const size_t grow = align_up(need, 1 << 20);
+  if (ctx->budget && ctx->used - ctx->ws_bytes + grow > ctx->budget) return LSG_E_BUDGET;
+  if (ctx->ws) {
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_status(e);
+    cudaFree(ctx->ws);
+    ctx->used -= ctx->ws_bytes;
+    ctx->ws = nullptr;
+    ctx->ws_bytes = 0;
+  }
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, grow);
+  if (e != cudaSuccess) return cuda_status(e);
+  ctx->ws = p;
+  ctx->ws_bytes = grow;
+  ctx->used += grow;
+  return LSG_OK;
+}
+
+lsg_status run_pass(const KArgs& a, int tile, bool geometry, cudaStream_t st) {
+  cudaError_t e = launch_prep(a, st);
+  if (e == cudaSuccess) e = geometry ? launch_tile(tile, a, st) : launch_tile_ccl(tile, a, st);
+  if (e == cudaSuccess) e = launch_merge(tile, a, st);
+  if (e == cudaSuccess) e = launch_flatten(tile, a, st);
+  return cuda_status(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+void lsg_default_params(lsg_params* p) {
+  if (!p) return;
+  p->subsample = 1;
+  p->r_min = 0.f;
+  p->r_max = 100.f;
+  p->jump_rel_h = 0.10f;
+  p->jump_rel_v = 1.0f;
+  p->predicate = LSG_PRED_ANGLE;
+  p->angle_rad = (float)(10.0 * 3.14159265358979323846 / 180.0);
+  p->comp[0] = p->comp[1] = p->comp[2] = 0.2f;
+  p->wrap = 1;
+}
+
+const char* lsg_status_str(lsg_status s) {
+  switch (s) {
+    case LSG_OK: return "ok";
+    case LSG_E_ARG: return "invalid argument";
+    case LSG_E_SHAPE: return "invalid scan shape";
+    case LSG_E_OOM: return "device allocation failed";
+    case LSG_E_BUDGET: return "memory budget exceeded";
+    case LSG_E_CUDA: return "CUDA runtime error";
+    case LSG_E_TIMEOUT: return "bounded device wait ran out";
+    case LSG_E_DEVICE: return "device flagged bad input";
+  }
+  return "unknown status";
+}
+
+lsg_status lsg_create(int device, size_t mem_budget_bytes, lsg_ctx** out) {
+  if (!out) return LSG_E_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return LSG_E_ARG;
+  DeviceGuard g(device);
+  cudaError_t e = prepare_kernels();
+  if (e != cudaSuccess) return cuda_status(e);
+  lsg_ctx* c = new (std::nothrow) lsg_ctx();
+  if (!c) return LSG_E_OOM;
+  c->device = device;
+  c->budget = mem_budget_bytes;
+  e = cudaMalloc(&c->d_err, 256);
+  if (e != cudaSuccess) {
+    delete c;
+    return cuda_status(e);
+  }
+  c->used = 256;
+  e = cudaMemset(c->d_err, 0, sizeof(int32_t));
+  if (e != cudaSuccess) {
+    cudaFree(c->d_err);
+    delete c;
+    return cuda_status(e);
+  }
+  *out = c;
+  return LSG_OK;
+}
+
+lsg_status lsg_destroy(lsg_ctx* ctx) {
+  if (!ctx) return LSG_E_ARG;
+  DeviceGuard g(ctx->device);
+  cudaDeviceSynchronize();
+  if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->d_err) cudaFree(ctx->d_err);
+  delete ctx;
+  return LSG_OK;
+}
+
+lsg_status lsg_set_tile(lsg_ctx* ctx, int tile) {
+  if (!ctx) return LSG_E_ARG;
+  if (tile == LSG_TILE_AUTO) tile = LSG_TILE_8x128;
+  if (tile < 0 || tile >= LSG_TILE_COUNT) return LSG_E_ARG;
+  ctx->tile = tile;
+  return LSG_OK;
+}
+
+lsg_status lsg_segment(lsg_ctx* ctx, const lsg_scan* scan, const lsg_params* params,
+                       const lsg_out* out, lsg_stream stream) {
+  if (!ctx) return LSG_E_ARG;
+  int Ws = 0;
+  lsg_status st = check_scan(scan, params, out, &Ws);
+  if (st != LSG_OK) return st;
+  DeviceGuard g(ctx->device);
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+  if (scan->rings == 0 || scan->cols == 0)
+    return cuda_status(cudaMemsetAsync(out->nseg, 0, sizeof(int32_t), cs));
+  st = reserve(ctx, scan_ws_bytes(scan->rings, Ws));
+  if (st != LSG_OK) return st;
+  KArgs a;
+  memset(&a, 0, sizeof(a));
+  a.one = make_desc(scan, params, out, Ws);
+  set_tiles(a.one, ctx->tile, 0);
+  carve_ws(a.one, static_cast<char*>(ctx->ws));
+  a.ntiles = a.one.tiles_r * a.one.tiles_c;
+  a.nscans = 1;
+  a.err = ctx->d_err;
+  return run_pass(a, ctx->tile, true, cs);
+}
+
+lsg_status lsg_label_from_mask(lsg_ctx* ctx, int32_t H, int32_t W, int32_t s, int32_t wrap,
+                               const uint8_t* meshbits, const uint8_t* valid, int32_t* labels,
+                               int32_t* nseg, lsg_stream stream) {
+  if (!ctx || !nseg) return LSG_E_ARG;
+  if (H < 0 || W < 0 || H > LSG_MAX_RINGS || W > LSG_MAX_COLS) return LSG_E_SHAPE;
+  if ((int64_t)H * W > (int64_t)LSG_MAX_POINTS) return LSG_E_SHAPE;
+  if (s < 1) return LSG_E_ARG;
+  DeviceGuard g(ctx->device);
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+  if (H == 0 || W == 0) return cuda_status(cudaMemsetAsync(nseg, 0, sizeof(int32_t), cs));
+  if (!meshbits || !labels || (s > 1 && !valid)) return LSG_E_ARG;
+  const int Ws = (W + s - 1) / s;
+  lsg_status st = reserve(ctx, scan_ws_bytes(H, Ws));
+  if (st != LSG_OK) return st;
+  KArgs a;
+  memset(&a, 0, sizeof(a));
+  ScanDesc& d = a.one;
+  d.H = H;
+  d.W = W;
+  d.Ws = Ws;
+  d.s = s;
+  d.wrap = (wrap && Ws >= 3) ? 1 : 0;
+  d.mb = const_cast<uint8_t*>(meshbits);
+  d.valid = valid;
+  d.labels = labels;
+  d.nseg = nseg;
+  set_tiles(d, ctx->tile, 0);
+  carve_ws(d, static_cast<char*>(ctx->ws));
+  a.ntiles = d.tiles_r * d.tiles_c;
+  a.nscans = 1;
+  a.err = ctx->d_err;
+  // no elevations: the ring order is the identity and only nseg is reset
+  cudaError_t e = cudaMemsetAsync(nseg, 0, sizeof(int32_t), cs);
+  if (e == cudaSuccess) e = launch_tile_ccl(ctx->tile, a, cs);
+  if (e == cudaSuccess) e = launch_merge(ctx->tile, a, cs);
+  if (e == cudaSuccess) e = launch_flatten(ctx->tile, a, cs);
+  return cuda_status(e);
+}
+
+lsg_status lsg_get_error(lsg_ctx* ctx) {
+  if (!ctx) return LSG_E_ARG;
+  DeviceGuard g(ctx->device);
+  int32_t v = 0;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_status(e);
+  e = cudaMemcpy(&v, ctx->d_err, sizeof(v), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_status(e);
+  cudaMemset(ctx->d_err, 0, sizeof(int32_t));
+  if (v & DERR_TIMEOUT) return LSG_E_TIMEOUT;
+  if (v) return LSG_E_DEVICE;
+  return LSG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batched path
+// ---------------------------------------------------------------------------
+static lsg_status plan_layout(lsg_plan* pl, int tile) {
+  // tile fields of every descriptor + the tile -> scan table, on the host
+  std::vector<int32_t> ts;
+  int32_t t0 = 0;
+  for (int b = 0; b < pl->n; ++b) {
+    ScanDesc& d = pl->host_desc[b];
+    set_tiles(d, tile, t0);
+    const int nt = (d.H && d.W) ? d.tiles_r * d.tiles_c : 0;
+    for (int k = 0; k < nt; ++k) ts.push_back(b);
+    t0 += nt;
+  }
+  pl->ntiles = t0;
+  if (pl->d_tile_scan) cudaFree(pl->d_tile_scan);
+  pl->d_tile_scan = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (t0 > 0) {
+    e = cudaMalloc(&pl->d_tile_scan, sizeof(int32_t) * t0);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(pl->d_tile_scan, ts.data(), sizeof(int32_t) * t0, cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpy(pl->d_desc, pl->host_desc.data(), sizeof(ScanDesc) * pl->n, cudaMemcpyHostToDevice);
+  pl->tile = tile;
+  return cuda_status(e);
+}
+
+static lsg_status plan_capture(lsg_plan* pl) {
+  if (pl->exec) cudaGraphExecDestroy(pl->exec);
+  if (pl->graph) cudaGraphDestroy(pl->graph);
+  pl->exec = nullptr;
+  pl->graph = nullptr;
+  cudaStream_t cs;
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_status(e);
+  KArgs a;
+  memset(&a, 0, sizeof(a));
+  a.scans = pl->d_desc;
+  a.tile_scan = pl->d_tile_scan;
+  a.ntiles = pl->ntiles;
+  a.nscans = pl->n;
+  a.err = pl->ctx->d_err;
+  for (int k = 0; k < 5 && e == cudaSuccess; ++k)
+    if (!pl->ev[k]) e = cudaEventCreate(&pl->ev[k]);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  lsg_status st = LSG_OK;
+  if (e == cudaSuccess) {
+    // scans with no points only get their counter cleared (by k_prep, which
+    // runs one block per scan); the tile kernels see only non-empty scans.
+    // Event-record nodes between the phases give per-kernel device times.
+    cudaError_t le = cudaEventRecord(pl->ev[0], cs);
+    if (le == cudaSuccess) le = launch_prep(a, cs);
+    if (le == cudaSuccess) le = cudaEventRecord(pl->ev[1], cs);
+    if (le == cudaSuccess && pl->ntiles > 0) le = launch_tile(pl->tile, a, cs);
+    if (le == cudaSuccess) le = cudaEventRecord(pl->ev[2], cs);
+    if (le == cudaSuccess && pl->ntiles > 0) le = launch_merge(pl->tile, a, cs);
+    if (le == cudaSuccess) le = cudaEventRecord(pl->ev[3], cs);
+    if (le == cudaSuccess && pl->ntiles > 0) le = launch_flatten(pl->tile, a, cs);
+    if (le == cudaSuccess) le = cudaEventRecord(pl->ev[4], cs);
+    e = cudaStreamEndCapture(cs, &pl->graph);
+    if (le != cudaSuccess) e = le;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&pl->exec, pl->graph, 0);
+  st = cuda_status(e);
+  cudaStreamDestroy(cs);
+  return st;
+}
+
+lsg_status lsg_batch_plan(lsg_ctx* ctx, int32_t n, const lsg_scan* scans, const lsg_params* params,
+                          const lsg_out* outs, int tile, lsg_plan** plan) {
+  if (!ctx || !plan || n < 1 || !scans || !params || !outs) return LSG_E_ARG;
+  *plan = nullptr;
+  if (tile == LSG_TILE_AUTO) tile = ctx->tile;
+  if (tile < 0 || tile >= LSG_TILE_COUNT) return LSG_E_ARG;
+  std::vector<int> Ws(n);
+  size_t ws_total = 0;
+  for (int b = 0; b < n; ++b) {
+    lsg_status st = check_scan(&scans[b], &params[b], &outs[b], &Ws[b]);
+    if (st != LSG_OK) return st;
+    ws_total += scan_ws_bytes(scans[b].rings, Ws[b]);
+  }
+  // the tile table is largest for the smallest tile (8 x 64 vertices)
+  size_t tiles_max = 0;
+  for (int b = 0; b < n; ++b)
+    tiles_max += (size_t)((scans[b].rings + 1) / 2 + 1) * ((Ws[b] + 63) / 64 + 1);
+  const size_t bytes = ws_total + align_up(sizeof(ScanDesc) * n, 256) + sizeof(int32_t) * tiles_max;
+  if (ctx->budget && ctx->used + bytes > ctx->budget) return LSG_E_BUDGET;
+  DeviceGuard g(ctx->device);
+  lsg_plan* pl = new (std::nothrow) lsg_plan();
+  if (!pl) return LSG_E_OOM;
+  pl->ctx = ctx;
+  pl->n = n;
+  pl->host_desc.resize(n);
+  cudaError_t e = cudaMalloc(&pl->ws, ws_total > 0 ? ws_total : 256);
+  if (e == cudaSuccess) e = cudaMalloc(&pl->d_desc, sizeof(ScanDesc) * n);
+  if (e != cudaSuccess) {
+    if (pl->ws) cudaFree(pl->ws);
+    delete pl;
+    return cuda_status(e);
+  }
+  char* base = static_cast<char*>(pl->ws);
+  for (int b = 0; b < n; ++b) {
+    ScanDesc d = make_desc(&scans[b], &params[b], &outs[b], Ws[b]);
+    carve_ws(d, base);
+    base += scan_ws_bytes(d.H, d.Ws);
+    pl->host_desc[b] = d;
+  }
+  pl->bytes = bytes;
+  ctx->used += bytes;
+  lsg_status st = plan_layout(pl, tile);
+  if (st == LSG_OK) st = plan_capture(pl);
+  if (st != LSG_OK) {
+    lsg_plan_destroy(pl);
+    return st;
+  }
+  *plan = pl;
+  return LSG_OK;
+}
+
+lsg_status lsg_batch_run(lsg_plan* plan, lsg_stream stream) {
+  if (!plan || !plan->exec) return LSG_E_ARG;
+  DeviceGuard g(plan->ctx->device);
+  return cuda_status(cudaGraphLaunch(plan->exec, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+int lsg_plan_tile(const lsg_plan* plan) { return plan ? plan->tile : -1; }
+
+lsg_status lsg_plan_phase_times(lsg_plan* plan, float* ms) {
+  if (!plan || !ms || !plan->ev[4]) return LSG_E_ARG;
+  DeviceGuard g(plan->ctx->device);
+  cudaError_t e = cudaEventSynchronize(plan->ev[4]);
+  for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventElapsedTime(&ms[k], plan->ev[k], plan->ev[k + 1]);
+  return cuda_status(e);
+}
+
+lsg_status lsg_autotune(lsg_plan* plan, int reps, lsg_stream stream, int* best_tile, float* best_ms) {
+  if (!plan || reps < 1) return LSG_E_ARG;
+  DeviceGuard g(plan->ctx->device);
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return LSG_E_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return LSG_E_CUDA;
+  }
+  int best = plan->tile;
+  float best_t = INFINITY;
+  lsg_status st = LSG_OK;
+  for (int t = 0; t < LSG_TILE_COUNT && st == LSG_OK; ++t) {
+    st = plan_layout(plan, t);
+    if (st == LSG_OK) st = plan_capture(plan);
+    if (st != LSG_OK) break;
+    cudaGraphLaunch(plan->exec, cs);  // warm-up
+    cudaEventRecord(e0, cs);
+    for (int r = 0; r < reps; ++r) cudaGraphLaunch(plan->exec, cs);
+    cudaEventRecord(e1, cs);
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) {
+      st = cuda_status(e);
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= reps;
+    if (ms < best_t) {
+      best_t = ms;
+      best = t;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st == LSG_OK) st = plan_layout(plan, best);
+  if (st == LSG_OK) st = plan_capture(plan);
+  if (best_tile) *best_tile = best;
+  if (best_ms) *best_ms = best_t;
+  return st;
+}
+
+lsg_status lsg_plan_destroy(lsg_plan* plan) {
+  if (!plan) return LSG_E_ARG;
+  DeviceGuard g(plan->ctx->device);
+  cudaDeviceSynchronize();
+  if (plan->exec) cudaGraphExecDestroy(plan->exec);
+  if (plan->graph) cudaGraphDestroy(plan->graph);
+  for (int k = 0; k < 5; ++k)
+    if (plan->ev[k]) cudaEventDestroy(plan->ev[k]);
+  if (plan->d_tile_scan) cudaFree(plan->d_tile_scan);
+  if (plan->d_desc) cudaFree(plan->d_desc);
+  if (plan->ws) cudaFree(plan->ws);
+  plan->ctx->used -= plan->bytes;
+  delete plan;
+  return LSG_OK;
+}
+
+}  // extern "C"

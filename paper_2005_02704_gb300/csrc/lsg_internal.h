@@ -1,0 +1,63 @@
+// lsg_internal.h - descriptors and kernel launchers shared by the library's
+// translation units (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/lsg.h"
+
+namespace lsg {
+
+// Everything one kernel needs to know about one scan.  Built on the host,
+// passed by value (single scan) or in a device table (batched pass).
+struct ScanDesc {
+  // inputs
+  const float4* xyzr;   // [H][W] (input ring order) or null
+  const float* range;   // [H][W] when xyzr is null
+  const float* elev;    // [H]
+  const uint8_t* valid; // [H][W] sorted order; label-from-mask path only
+  // outputs
+  uint8_t* mb;          // [H][Ws]
+  float* nrm;           // [H][Ws][3]
+  int32_t* labels;      // [H][W]
+  int32_t* nseg;        // [1]
+  // workspace
+  int32_t* order;       // [H]   sorted ring -> input row
+  float2* trig;         // [H]   (sin, cos) of the sorted ring's elevation
+  int32_t* parent;      // [H*Ws] union-find over scan-local vertex indices
+  // shape
+  int32_t H, W, Ws, s, wrap;  // wrap already reduced to (wrap && Ws >= 3)
+  int32_t tiles_r, tiles_c, tile0;
+  // parameters
+  float az0, daz, r_min, r_max, jump_h, jump_v;
+  float cos_t, comp_x, comp_y, comp_z, nsign;
+  int32_t pred;
+};
+
+struct KArgs {
+  const ScanDesc* scans;     // device table, or null: use `one`
+  const int32_t* tile_scan;  // device [ntiles] tile -> scan (batched), or null
+  int32_t ntiles;
+  int32_t nscans;
+  int32_t* err;              // device error word
+  ScanDesc one;
+};
+
+// Device error codes (sticky, OR-ed into *err).
+enum : int32_t { DERR_NAN_ELEV = 1, DERR_TIMEOUT = 2 };
+
+struct TileShape {
+  int rows, cols;
+};
+TileShape tile_shape(int tile);
+
+// Kernel launchers (lsg_kernels.cu).  All return the launch error.
+cudaError_t launch_prep(const KArgs& a, cudaStream_t st);
+cudaError_t launch_tile(int tile, const KArgs& a, cudaStream_t st);
+cudaError_t launch_tile_ccl(int tile, const KArgs& a, cudaStream_t st);
+cudaError_t launch_merge(int tile, const KArgs& a, cudaStream_t st);
+cudaError_t launch_flatten(int tile, const KArgs& a, cudaStream_t st);
+cudaError_t prepare_kernels();  // one-time function attributes
+
+}  // namespace lsg

@@ -1,0 +1,333 @@
+"""Python binding of the C ABI in ``include/lsg.h`` (ctypes; argument
+marshalling only).
+
+The functions keep the C names (``lsg_segment``, ``lsg_batch_plan``, ...) and
+take raw device pointers; ``Context`` is a thin convenience layer that
+allocates outputs with PyTorch (device memory and streams only) and calls the
+same entry points.  Every step of the path runs in the library's CUDA
+kernels; there is no CPU fallback, and ``load()`` raises when the library
+cannot be built or loaded.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+from dataclasses import dataclass
+from typing import List, Optional, Sequence
+
+from . import _build
+
+LSG_OK, LSG_E_ARG, LSG_E_SHAPE, LSG_E_OOM, LSG_E_BUDGET, LSG_E_CUDA, LSG_E_TIMEOUT, LSG_E_DEVICE = range(8)
+LSG_PRED_ANGLE, LSG_PRED_COMPONENT = 0, 1
+LSG_TILE_AUTO = -1
+TILES = {"8x128": 0, "4x256": 1, "16x64": 2, "2x512": 3, "8x64": 4}
+LSG_TILE_COUNT = len(TILES)
+
+BIT_R, BIT_D, BIT_G = 0x01, 0x02, 0x04
+BIT_HR, BIT_HD, BIT_HG = 0x08, 0x10, 0x20
+BIT_VALID, BIT_HASN = 0x40, 0x80
+
+
+class lsg_scan(ctypes.Structure):
+    _fields_ = [("rings", ctypes.c_int32), ("cols", ctypes.c_int32), ("elevation", ctypes.c_void_p),
+                ("azimuth0", ctypes.c_float), ("azimuth_step", ctypes.c_float),
+                ("xyzr", ctypes.c_void_p), ("range", ctypes.c_void_p)]
+
+
+class lsg_params(ctypes.Structure):
+    _fields_ = [("subsample", ctypes.c_int32), ("r_min", ctypes.c_float), ("r_max", ctypes.c_float),
+                ("jump_rel_h", ctypes.c_float), ("jump_rel_v", ctypes.c_float),
+                ("predicate", ctypes.c_int32), ("angle_rad", ctypes.c_float),
+                ("comp", ctypes.c_float * 3), ("wrap", ctypes.c_int32)]
+
+
+class lsg_out(ctypes.Structure):
+    _fields_ = [("meshbits", ctypes.c_void_p), ("normals", ctypes.c_void_p),
+                ("labels", ctypes.c_void_p), ("nseg", ctypes.c_void_p)]
+
+
+class LsgError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {lsg_status_str(status)} ({status})")
+        self.status = status
+
+
+_lib = None
+_P = ctypes.c_void_p
+
+
+def load(build: bool = True):
+    """Load ``liblsg.so`` (building it in-tree first when it is stale)."""
+    global _lib
+    if _lib is None:
+        path = _build.build() if build else _build.LIB
+        lib = ctypes.CDLL(path)
+        I32 = ctypes.c_int32
+        sig = {
+            "lsg_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t, ctypes.POINTER(_P)]),
+            "lsg_destroy": (ctypes.c_int, [_P]),
+            "lsg_set_tile": (ctypes.c_int, [_P, ctypes.c_int]),
+            "lsg_segment": (ctypes.c_int, [_P, ctypes.POINTER(lsg_scan), ctypes.POINTER(lsg_params),
+                                           ctypes.POINTER(lsg_out), _P]),
+            "lsg_label_from_mask": (ctypes.c_int, [_P, I32, I32, I32, I32, _P, _P, _P, _P, _P]),
+            "lsg_batch_plan": (ctypes.c_int, [_P, I32, ctypes.POINTER(lsg_scan), ctypes.POINTER(lsg_params),
+                                              ctypes.POINTER(lsg_out), ctypes.c_int, ctypes.POINTER(_P)]),
+            "lsg_batch_run": (ctypes.c_int, [_P, _P]),
+            "lsg_autotune": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_int),
+                                            ctypes.POINTER(ctypes.c_float)]),
+            "lsg_plan_tile": (ctypes.c_int, [_P]),
+            "lsg_plan_phase_times": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float)]),
+            "lsg_plan_destroy": (ctypes.c_int, [_P]),
+            "lsg_get_error": (ctypes.c_int, [_P]),
+            "lsg_default_params": (None, [ctypes.POINTER(lsg_params)]),
+            "lsg_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+# ---- the C entry points, same names -------------------------------------
+def lsg_status_str(status: int) -> str:
+    return load().lsg_status_str(status).decode()
+
+
+def _check(status: int, what: str):
+    if status != LSG_OK:
+        raise LsgError(status, what)
+
+
+def lsg_default_params() -> lsg_params:
+    p = lsg_params()
+    load().lsg_default_params(ctypes.byref(p))
+    return p
+
+
+def lsg_create(device: int = 0, budget_bytes: int = 0) -> int:
+    h = _P()
+    _check(load().lsg_create(device, budget_bytes, ctypes.byref(h)), "lsg_create")
+    return h.value
+
+
+def lsg_destroy(ctx: int) -> None:
+    _check(load().lsg_destroy(ctx), "lsg_destroy")
+
+
+def lsg_set_tile(ctx: int, tile: int) -> None:
+    _check(load().lsg_set_tile(ctx, tile), "lsg_set_tile")
+
+
+def lsg_segment(ctx: int, scan: lsg_scan, params: lsg_params, out: lsg_out, stream: int = 0) -> int:
+    """Returns the status code (callers that want exceptions use Context)."""
+    return load().lsg_segment(ctx, ctypes.byref(scan), ctypes.byref(params), ctypes.byref(out), stream or None)
+
+
+def lsg_label_from_mask(ctx: int, H: int, W: int, s: int, wrap: int, meshbits: int, valid: int,
+                        labels: int, nseg: int, stream: int = 0) -> int:
+    return load().lsg_label_from_mask(ctx, H, W, s, wrap, meshbits or None, valid or None, labels or None,
+                                      nseg or None, stream or None)
+
+
+def lsg_batch_plan(ctx: int, scans: Sequence[lsg_scan], params: Sequence[lsg_params],
+                   outs: Sequence[lsg_out], tile: int = LSG_TILE_AUTO) -> int:
+    n = len(scans)
+    sa = (lsg_scan * n)(*scans)
+    pa = (lsg_params * n)(*params)
+    oa = (lsg_out * n)(*outs)
+    h = _P()
+    _check(load().lsg_batch_plan(ctx, n, sa, pa, oa, tile, ctypes.byref(h)), "lsg_batch_plan")
+    return h.value
+
+
+def lsg_batch_run(plan: int, stream: int = 0) -> int:
+    return load().lsg_batch_run(plan, stream or None)
+
+
+def lsg_autotune(plan: int, reps: int = 3, stream: int = 0):
+    t = ctypes.c_int()
+    ms = ctypes.c_float()
+    _check(load().lsg_autotune(plan, reps, stream or None, ctypes.byref(t), ctypes.byref(ms)), "lsg_autotune")
+    return t.value, ms.value
+
+
+def lsg_plan_tile(plan: int) -> int:
+    return load().lsg_plan_tile(plan)
+
+
+def lsg_plan_phase_times(plan: int):
+    ms = (ctypes.c_float * 4)()
+    _check(load().lsg_plan_phase_times(plan, ms), "lsg_plan_phase_times")
+    return list(ms)
+
+
+def lsg_plan_destroy(plan: int) -> None:
+    _check(load().lsg_plan_destroy(plan), "lsg_plan_destroy")
+
+
+def lsg_get_error(ctx: int) -> int:
+    return load().lsg_get_error(ctx)
+
+
+# ---- convenience layer (torch for device memory and streams) -------------
+@dataclass
+class Params:
+    """Python mirror of lsg_params with the library's defaults."""
+    subsample: int = 1
+    r_min: float = 0.0
+    r_max: float = 100.0
+    jump_rel_h: float = 0.10
+    jump_rel_v: float = 1.0
+    predicate: int = LSG_PRED_ANGLE
+    angle_rad: float = math.radians(10.0)
+    comp: Sequence[float] = (0.2, 0.2, 0.2)
+    wrap: int = 1
+
+    def to_c(self) -> lsg_params:
+        p = lsg_params()
+        p.subsample = int(self.subsample)
+        p.r_min = float(self.r_min)
+        p.r_max = float(self.r_max)
+        p.jump_rel_h = float(self.jump_rel_h)
+        p.jump_rel_v = float(self.jump_rel_v)
+        p.predicate = int(self.predicate)
+        p.angle_rad = float(self.angle_rad)
+        for k in range(3):
+            p.comp[k] = float(self.comp[k])
+        p.wrap = int(self.wrap)
+        return p
+
+
+@dataclass
+class Outputs:
+    meshbits: "torch.Tensor"  # uint8 [H, Ws]
+    normals: "torch.Tensor"   # float32 [H, Ws, 3]
+    labels: "torch.Tensor"    # int32 [H, W]
+    nseg: "torch.Tensor"      # int32 [1]
+
+    def to_c(self) -> lsg_out:
+        o = lsg_out()
+        o.meshbits = self.meshbits.data_ptr() if self.meshbits.numel() else None
+        o.normals = self.normals.data_ptr() if self.normals.numel() else None
+        o.labels = self.labels.data_ptr() if self.labels.numel() else None
+        o.nseg = self.nseg.data_ptr()
+        return o
+
+
+def ws_of(W: int, s: int) -> int:
+    return (W + s - 1) // s if W else 0
+
+
+def alloc_outputs(H: int, W: int, s: int, device) -> Outputs:
+    import torch
+    Ws = ws_of(W, s)
+    return Outputs(torch.empty((H, Ws), dtype=torch.uint8, device=device),
+                   torch.empty((H, Ws, 3), dtype=torch.float32, device=device),
+                   torch.empty((H, W), dtype=torch.int32, device=device),
+                   torch.zeros(1, dtype=torch.int32, device=device))
+
+
+def make_scan(elev, xyzr=None, range_=None, az0: float = 0.0, daz: float = 0.0) -> lsg_scan:
+    """lsg_scan over device tensors (elev float32 [H]; xyzr float32 [H, W, 4]
+    or range float32 [H, W])."""
+    sc = lsg_scan()
+    src = xyzr if xyzr is not None else range_
+    sc.rings = int(src.shape[0])
+    sc.cols = int(src.shape[1]) if src.dim() > 1 else 0
+    sc.elevation = elev.data_ptr() if elev.numel() else None
+    sc.azimuth0 = float(az0)
+    sc.azimuth_step = float(daz)
+    sc.xyzr = xyzr.data_ptr() if (xyzr is not None and xyzr.numel()) else None
+    sc.range = range_.data_ptr() if (range_ is not None and range_.numel()) else None
+    return sc
+
+
+def _stream_ptr(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+class Context:
+    """Owns an lsg context on one device."""
+
+    def __init__(self, device: int = 0, budget_bytes: int = 0, tile: Optional[int] = None):
+        self.device = device
+        self.h = lsg_create(device, budget_bytes)
+        if tile is not None:
+            lsg_set_tile(self.h, tile)
+
+    def close(self):
+        if self.h:
+            lsg_destroy(self.h)
+            self.h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def segment(self, elev, xyzr=None, range_=None, az0=0.0, daz=0.0, params: Params = Params(),
+                out: Optional[Outputs] = None, stream=None) -> Outputs:
+        src = xyzr if xyzr is not None else range_
+        H, W = int(src.shape[0]), int(src.shape[1])
+        if out is None:
+            out = alloc_outputs(H, W, params.subsample, src.device)
+        st = lsg_segment(self.h, make_scan(elev, xyzr, range_, az0, daz), params.to_c(), out.to_c(),
+                         _stream_ptr(stream))
+        _check(st, "lsg_segment")
+        return out
+
+    def label_from_mask(self, meshbits, valid, W: int, s: int, wrap: int, stream=None):
+        import torch
+        H = int(meshbits.shape[0])
+        labels = torch.empty((H, W), dtype=torch.int32, device=meshbits.device)
+        nseg = torch.zeros(1, dtype=torch.int32, device=meshbits.device)
+        st = lsg_label_from_mask(self.h, H, W, s, wrap, meshbits.data_ptr() if meshbits.numel() else 0,
+                                 valid.data_ptr() if (valid is not None and valid.numel()) else 0,
+                                 labels.data_ptr() if labels.numel() else 0, nseg.data_ptr(),
+                                 _stream_ptr(stream))
+        _check(st, "lsg_label_from_mask")
+        return labels, nseg
+
+    def error(self) -> int:
+        return lsg_get_error(self.h)
+
+
+class BatchPlan:
+    """A captured batched pass over fixed device buffers."""
+
+    def __init__(self, ctx: Context, scans: List[lsg_scan], params: List[lsg_params], outs: List[lsg_out],
+                 tile: int = LSG_TILE_AUTO):
+        self.ctx = ctx
+        self._keep = (scans, params, outs)
+        self.h = lsg_batch_plan(ctx.h, scans, params, outs, tile)
+
+    def run(self, stream=None):
+        _check(lsg_batch_run(self.h, _stream_ptr(stream)), "lsg_batch_run")
+
+    def autotune(self, reps: int = 3, stream=None):
+        return lsg_autotune(self.h, reps, _stream_ptr(stream))
+
+    @property
+    def tile(self) -> int:
+        return lsg_plan_tile(self.h)
+
+    def phase_times(self):
+        """[ring order, tile kernel, border merge, labels] ms of the last replay."""
+        return lsg_plan_phase_times(self.h)
+
+    def close(self):
+        if self.h:
+            lsg_plan_destroy(self.h)
+            self.h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,132 @@
+"""GPU tests of the batched path: one captured pass over many uneven scans
+equals the per-scan path bit for bit, the autotuner keeps results, and the
+benchmark workload (512 scans) matches the oracle on sampled scans and on
+every scan's labels given its own mask."""
+import math
+
+import numpy as np
+import pytest
+
+import lidarsim
+import oracle as O
+import parity
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def mods():
+    from paper_2005_02704_gb300 import batch, lsg
+    return lsg, batch
+
+
+def params_of(spec):
+    lsg, _ = mods()
+    return lsg.Params(subsample=spec.subsample, r_max=spec.r_max, jump_rel_h=spec.jump_rel_h,
+                      jump_rel_v=spec.jump_rel_v, angle_rad=math.radians(spec.angle_deg))
+
+
+def make_batch(specs, scans):
+    lsg, batch = mods()
+    shapes = [batch.ScanShape(s.rings, s.cols, sp.subsample) for sp, s in zip(specs, scans)]
+    db = batch.DeviceBatch(shapes, [params_of(sp) for sp in specs], 0)
+    for b, s in enumerate(scans):
+        db.set_scan(b, s)
+    db.upload()
+    torch.cuda.synchronize()
+    return db
+
+
+@pytest.fixture(scope="module")
+def ctx(gpu_lib):
+    lsg, _ = mods()
+    c = lsg.Context(0)
+    yield c
+    c.close()
+
+
+def mixed_specs(n, seed0):
+    specs = lidarsim.batch_specs(n, seed0)
+    # add sub-sampling, no-wrap-sized and tiny scans to the mix
+    from dataclasses import replace
+    specs[1] = replace(specs[1], subsample=3)
+    specs[2] = replace(specs[2], elev_deg=specs[2].elev_deg[:1], cols=5)
+    specs[3] = replace(specs[3], cols=2)
+    return specs
+
+
+@pytest.mark.parametrize("tile", ["8x128", "4x256", "16x64", "2x512", "8x64"])
+def test_batch_equals_per_scan(ctx, tile):
+    lsg, _ = mods()
+    specs = mixed_specs(12, 5000)
+    scans = [lidarsim.make_scan(sp) for sp in specs]
+    db = make_batch(specs, scans)
+    plan = db.plan(ctx, lsg.TILES[tile])
+    plan.run()
+    plan.run()  # replays are idempotent
+    torch.cuda.synchronize()
+    assert ctx.error() == lsg.LSG_OK
+    for b, (sp, s) in enumerate(zip(specs, scans)):
+        mb, nrm, lab, nseg = db.view(b)
+        elev, xyzr = db.scan_inputs(b)
+        out = ctx.segment(elev, xyzr=xyzr, az0=s.az0, daz=s.daz, params=params_of(sp))
+        torch.cuda.synchronize()
+        assert torch.equal(out.meshbits, mb)
+        assert torch.equal(out.normals, nrm)
+        assert torch.equal(out.labels, lab)
+        assert torch.equal(out.nseg, nseg)
+    plan.close()
+
+
+def test_autotune_keeps_results(ctx):
+    lsg, _ = mods()
+    specs = mixed_specs(8, 6000)
+    scans = [lidarsim.make_scan(sp) for sp in specs]
+    db = make_batch(specs, scans)
+    plan = db.plan(ctx)
+    plan.run()
+    torch.cuda.synchronize()
+    ref = (db.d_mb.clone(), db.d_nrm.clone(), db.d_lab.clone(), db.d_nseg.clone())
+    best, ms = plan.autotune(reps=2)
+    assert 0 <= best < lsg.LSG_TILE_COUNT and plan.tile == best and ms > 0
+    plan.run()
+    torch.cuda.synchronize()
+    for a, b in zip(ref, (db.d_mb, db.d_nrm, db.d_lab, db.d_nseg)):
+        assert torch.equal(a, b)
+    plan.close()
+
+
+def test_bench_workload_512_scans(ctx):
+    """The benchmark's batch (512 seeded scans, rings 16..128, widths
+    1024..4096) in the benchmark's launch configuration: sampled scans
+    against the full oracle; every scan's labels and segment count against
+    the oracle's components of the GPU's own mask."""
+    lsg, _ = mods()
+    specs = lidarsim.batch_specs(512)
+    scans = [lidarsim.make_scan(sp) for sp in specs]
+    db = make_batch(specs, scans)
+    plan = db.plan(ctx)
+    plan.run()
+    torch.cuda.synchronize()
+    assert ctx.error() == lsg.LSG_OK
+    mb_all = db.d_mb.cpu().numpy()
+    nrm_all = db.d_nrm.cpu().numpy()
+    lab_all = db.d_lab.cpu().numpy()
+    nseg_all = db.d_nseg.cpu().numpy()
+    for b, (sp, s) in enumerate(zip(specs, scans)):
+        H, W, Ws = s.rings, s.cols, lsg.ws_of(s.cols, sp.subsample)
+        v0, p0 = int(db.v_off[b]), int(db.pt_off[b])
+        mb = mb_all[v0:v0 + H * Ws].reshape(H, Ws)
+        lab = lab_all[p0:p0 + H * W].reshape(H, W)
+        order = O.ring_order(s.elev)
+        valid = parity.sorted_valid(s, params_of(sp), order)
+        want, n = O.label_from_mask(mb, valid, W, sp.subsample, 1)
+        assert np.array_equal(lab, want), b
+        assert nseg_all[b] == n
+        if b % 64 == 0:  # sampled full comparison
+            p = params_of(sp)
+            orc = O.segment_scan(s, parity.oracle_params(p))
+            bounds = parity.normal_bounds(orc)
+            nrm = nrm_all[v0:v0 + H * Ws].reshape(H, Ws, 3)
+            parity.compare_geometry(mb, nrm, orc, parity.oracle_params(p), bounds)
+    plan.close()
