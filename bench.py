@@ -382,7 +382,7 @@ def main():
         import oracle
         oracle.build()
         cores = host_cores()
-        r, pts, ns, dt = oracle_rate(specs, scans, 25e6, cores)
+        r, pts, ns, dt = oracle_rate(specs, scans, float(db.points), cores)
         cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{ns} of the 512 scans (every {math.ceil(len(scans) / ns)}th), {pts / 1e6:.1f} M points, "
                          f"{dt:.1f} s wall on {cores} threads"}
