@@ -243,6 +243,38 @@ lsg_status lsg_plan_destroy(lsg_plan* plan);
  * device).  LSG_OK when no device-side error was recorded. */
 lsg_status lsg_get_error(lsg_ctx* ctx);
 
+/* Largest scan (rings x sampled columns) lsg_segment_noalloc accepts. */
+#define LSG_NOALLOC_MAX_VERTICES (1 << 20)
+
+/*
+ * lsg_segment without any device allocation (the paper has no counterpart:
+ * this is a deployment variant of lsg_segment).
+ *
+ * For callers that cannot call cudaMalloc: a sensor thread with a hard
+ * latency budget (cudaMalloc / cudaFree can synchronise the device and take
+ * driver-wide locks) or a host framework that owns all device memory and
+ * forbids side allocations.  The caller still allocates and owns the inputs
+ * and outputs; the workspace is one fixed device array inside the library
+ * (about 4.3 MB on every device that loads the library, held until the
+ * process exits).
+ *
+ *   scan, params, out  as for lsg_segment; uses the current CUDA device and
+ *                      the 8x128 tile shape.  Outputs equal lsg_segment's.
+ *   returns LSG_E_SHAPE when rings * ceil(cols/subsample) exceeds
+ *   LSG_NOALLOC_MAX_VERTICES (nothing is launched), LSG_E_ARG / LSG_E_SHAPE
+ *   as lsg_segment for bad arguments, LSG_E_CUDA if a launch fails.
+ *
+ * The first call on each device looks up the array's device address (make
+ * it from a thread where that device is current).  Every call shares the one
+ * array and leaves its contents behind, so calls whose work overlaps on the
+ * GPU (different streams, or different host threads, without ordering
+ * between them) race and corrupt each other's results: order them on one
+ * stream.  Device-side flags (a NaN elevation) are not reported by this
+ * entry point.
+ */
+lsg_status lsg_segment_noalloc(const lsg_scan* scan, const lsg_params* params, const lsg_out* out,
+                               lsg_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -61,6 +61,10 @@ lsg_status cuda_status(cudaError_t e) {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+}  // namespace
+
+namespace lsg {
+
 // Validates one scan's shape and parameters; fills Ws.
 lsg_status check_scan(const lsg_scan* sc, const lsg_params* p, const lsg_out* o, int* Ws_out) {
   if (!sc || !p || !o) return LSG_E_ARG;
@@ -131,6 +135,10 @@ void set_tiles(ScanDesc& d, int tile, int tile0) {
   d.tiles_c = (d.Ws + ts.cols - 1) / ts.cols;
   d.tile0 = tile0;
 }
+
+}  // namespace lsg
+
+namespace {
 
 size_t scan_ws_bytes(int H, int Ws) {
   return align_up(sizeof(int32_t) * H, 256) + align_up(sizeof(float2) * H, 256) +
@@ -379,15 +387,15 @@ static lsg_status plan_capture(lsg_plan* pl) {
     // scans with no points only get their counter cleared (by k_prep, which
     // runs one block per scan); the tile kernels see only non-empty scans.
     // Event-record nodes between the phases give per-kernel device times.
-    cudaError_t le = cudaEventRecord(pl->ev[0], cs);
+    cudaError_t le = cudaEventRecordWithFlags(pl->ev[0], cs, cudaEventRecordExternal);
     if (le == cudaSuccess) le = launch_prep(a, cs);
-    if (le == cudaSuccess) le = cudaEventRecord(pl->ev[1], cs);
+    if (le == cudaSuccess) le = cudaEventRecordWithFlags(pl->ev[1], cs, cudaEventRecordExternal);
     if (le == cudaSuccess && pl->ntiles > 0) le = launch_tile(pl->tile, a, cs);
-    if (le == cudaSuccess) le = cudaEventRecord(pl->ev[2], cs);
+    if (le == cudaSuccess) le = cudaEventRecordWithFlags(pl->ev[2], cs, cudaEventRecordExternal);
     if (le == cudaSuccess && pl->ntiles > 0) le = launch_merge(pl->tile, a, cs);
-    if (le == cudaSuccess) le = cudaEventRecord(pl->ev[3], cs);
+    if (le == cudaSuccess) le = cudaEventRecordWithFlags(pl->ev[3], cs, cudaEventRecordExternal);
     if (le == cudaSuccess && pl->ntiles > 0) le = launch_flatten(pl->tile, a, cs);
-    if (le == cudaSuccess) le = cudaEventRecord(pl->ev[4], cs);
+    if (le == cudaSuccess) le = cudaEventRecordWithFlags(pl->ev[4], cs, cudaEventRecordExternal);
     e = cudaStreamEndCapture(cs, &pl->graph);
     if (le != cudaSuccess) e = le;
   }

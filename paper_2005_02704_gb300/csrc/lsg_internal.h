@@ -52,6 +52,11 @@ struct TileShape {
 };
 TileShape tile_shape(int tile);
 
+// Host helpers shared by the entry points (lsg_api.cu).
+lsg_status check_scan(const lsg_scan* sc, const lsg_params* p, const lsg_out* o, int* Ws_out);
+ScanDesc make_desc(const lsg_scan* sc, const lsg_params* p, const lsg_out* o, int Ws);
+void set_tiles(ScanDesc& d, int tile, int tile0);
+
 // Kernel launchers (lsg_kernels.cu).  All return the launch error.
 cudaError_t launch_prep(const KArgs& a, cudaStream_t st);
 cudaError_t launch_tile(int tile, const KArgs& a, cudaStream_t st);

@@ -1,0 +1,93 @@
+// lsg_noalloc.cu - lsg_segment_noalloc: the single-scan pass of lsg_segment
+// for callers that must not allocate device memory.
+//
+// Who needs it: a sensor driver thread with a hard latency budget cannot
+// afford cudaMalloc/cudaFree on its path (they can synchronise the whole
+// device and take driver-wide locks, so their cost is unbounded), and some
+// host frameworks hand out every byte of device memory themselves and forbid
+// side allocations by their plug-ins.  Such callers can still own their input
+// and output buffers but cannot let the library grow a workspace.
+//
+// How: the workspace (ring order, per-ring sin/cos, union-find parents and a
+// device error word) lives in one file-scope __device__ array of fixed size,
+// created when the library is loaded on a device and held until the process
+// exits.  Host code cannot use the array's name as a device address, so the
+// first call on each device looks the address up with cudaGetSymbolAddress
+// (with that device current) and every call passes that pointer to the same
+// kernels lsg_segment uses.  No call allocates or frees anything.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "lsg_internal.h"
+
+namespace {
+
+// Layout of the fixed workspace (byte offsets, each 256-byte aligned).
+constexpr size_t kOrderOff = 0;                                         // int32[LSG_MAX_RINGS]
+constexpr size_t kTrigOff = kOrderOff + sizeof(int32_t) * LSG_MAX_RINGS;  // float2[LSG_MAX_RINGS]
+constexpr size_t kErrOff = kTrigOff + sizeof(float2) * LSG_MAX_RINGS;     // int32 error word
+constexpr size_t kParentOff = kErrOff + 256;                             // int32[max vertices]
+constexpr size_t kScratchBytes = kParentOff + sizeof(int32_t) * (size_t)LSG_NOALLOC_MAX_VERTICES;
+static_assert(kTrigOff % 256 == 0 && kErrOff % 256 == 0 && kParentOff % 256 == 0, "alignment");
+
+constexpr int kMaxDevices = 64;
+std::mutex g_setup_mu;
+void* g_scratch_addr[kMaxDevices] = {};
+
+}  // namespace
+
+// The workspace itself: one copy on every device that loads the library.
+static __device__ __align__(256) unsigned char g_lsg_scratch[kScratchBytes];
+
+// Device address of g_lsg_scratch on the current device; the lookup runs once
+// per device.
+static lsg_status scratch_for_current_device(char** base) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LSG_E_ARG;
+  std::lock_guard<std::mutex> lock(g_setup_mu);
+  if (!g_scratch_addr[dev]) {
+    if (lsg::prepare_kernels() != cudaSuccess) return LSG_E_CUDA;
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_lsg_scratch);
+    if (e != cudaSuccess || p == nullptr) return LSG_E_CUDA;
+    g_scratch_addr[dev] = p;
+  }
+  *base = static_cast<char*>(g_scratch_addr[dev]);
+  return LSG_OK;
+}
+
+extern "C" lsg_status lsg_segment_noalloc(const lsg_scan* scan, const lsg_params* params,
+                                          const lsg_out* out, lsg_stream stream) {
+  int Ws = 0;
+  lsg_status st = lsg::check_scan(scan, params, out, &Ws);
+  if (st != LSG_OK) return st;
+  if ((int64_t)scan->rings * Ws > (int64_t)LSG_NOALLOC_MAX_VERTICES) return LSG_E_SHAPE;
+  char* base = nullptr;
+  st = scratch_for_current_device(&base);
+  if (st != LSG_OK) return st;
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+  if (scan->rings == 0 || scan->cols == 0)
+    return cudaMemsetAsync(out->nseg, 0, sizeof(int32_t), cs) == cudaSuccess ? LSG_OK : LSG_E_CUDA;
+
+  lsg::KArgs a;
+  memset(&a, 0, sizeof(a));
+  a.one = lsg::make_desc(scan, params, out, Ws);
+  lsg::set_tiles(a.one, LSG_TILE_8x128, 0);
+  a.one.order = reinterpret_cast<int32_t*>(base + kOrderOff);
+  a.one.trig = reinterpret_cast<float2*>(base + kTrigOff);
+  a.one.parent = reinterpret_cast<int32_t*>(base + kParentOff);
+  a.ntiles = a.one.tiles_r * a.one.tiles_c;
+  a.nscans = 1;
+  a.err = reinterpret_cast<int32_t*>(base + kErrOff);
+  // The error word accumulates flags with atomicOr, so it must start at zero;
+  // everything else is fully written by the kernels before it is read.
+  cudaError_t e = cudaMemsetAsync(a.err, 0, sizeof(int32_t), cs);
+  if (e == cudaSuccess) e = lsg::launch_prep(a, cs);
+  if (e == cudaSuccess) e = lsg::launch_tile(LSG_TILE_8x128, a, cs);
+  if (e == cudaSuccess) e = lsg::launch_merge(LSG_TILE_8x128, a, cs);
+  if (e == cudaSuccess) e = lsg::launch_flatten(LSG_TILE_8x128, a, cs);
+  return e == cudaSuccess ? LSG_OK : LSG_E_CUDA;
+}

@@ -79,6 +79,8 @@ def load(build: bool = True):
             "lsg_plan_phase_times": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float)]),
             "lsg_plan_destroy": (ctypes.c_int, [_P]),
             "lsg_get_error": (ctypes.c_int, [_P]),
+            "lsg_segment_noalloc": (ctypes.c_int, [ctypes.POINTER(lsg_scan), ctypes.POINTER(lsg_params),
+                                                   ctypes.POINTER(lsg_out), _P]),
             "lsg_default_params": (None, [ctypes.POINTER(lsg_params)]),
             "lsg_status_str": (ctypes.c_char_p, [ctypes.c_int]),
         }
@@ -171,6 +173,16 @@ def lsg_get_error(ctx: int) -> int:
     return load().lsg_get_error(ctx)
 
 
+LSG_NOALLOC_MAX_VERTICES = 1 << 20
+
+
+def lsg_segment_noalloc(scan: lsg_scan, params: lsg_params, out: lsg_out, stream: int = 0) -> int:
+    """lsg_segment with its workspace in the library's fixed device array, for
+    callers that may not allocate device memory.  Returns the status code."""
+    return load().lsg_segment_noalloc(ctypes.byref(scan), ctypes.byref(params), ctypes.byref(out),
+                                      stream or None)
+
+
 # ---- convenience layer (torch for device memory and streams) -------------
 @dataclass
 class Params:
@@ -217,7 +229,9 @@ class Outputs:
 
 
 def ws_of(W: int, s: int) -> int:
-    return (W + s - 1) // s if W else 0
+    """Sampled columns ceil(W/s); 0 for an empty ring or an invalid s (which
+    the library then rejects)."""
+    return (W + s - 1) // s if (W > 0 and s >= 1) else 0
 
 
 def alloc_outputs(H: int, W: int, s: int, device) -> Outputs:
