@@ -61,6 +61,8 @@ class Report:
     vertices: int = 0
     ill_conditioned: int = 0
     max_err_well: float = 0.0
+    max_err_all: float = 0.0
+    frac_within_tol: float = 1.0
     edges: int = 0
     in_band: int = 0
     hasn_mismatch: int = 0
@@ -104,6 +106,8 @@ def compare_geometry(mb_g, nrm_g, orc: O.Result, p, bounds: np.ndarray, strict=T
     well = both & (bounds <= NORMAL_TOL)
     rep.ill_conditioned = int((both & ~well).sum())
     rep.max_err_well = float(err[well].max()) if well.any() else 0.0
+    rep.max_err_all = float(err[both].max()) if both.any() else 0.0
+    rep.frac_within_tol = float((err[both] <= NORMAL_TOL).mean()) if both.any() else 1.0
     if strict:
         assert rep.max_err_well <= NORMAL_TOL, f"normal error {rep.max_err_well} rad on a well-conditioned vertex"
         over = both & ~well & (err > bounds)
