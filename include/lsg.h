@@ -151,14 +151,16 @@ typedef struct {
   int32_t* nseg;
 } lsg_out;
 
-/* Tile shapes of the fused kernels (rows x columns of mesh vertices). */
+/* Tile shapes of the fused kernels: rows x columns of mesh vertices per CTA.
+ * Each warp of a CTA sweeps a strip of 29 columns down the tile's rows, so
+ * the widths are multiples of 29 (4 warps: 116, 8 warps: 232). */
 enum {
   LSG_TILE_AUTO = -1,
-  LSG_TILE_8x128 = 0,
-  LSG_TILE_4x256 = 1,
-  LSG_TILE_16x64 = 2,
-  LSG_TILE_2x512 = 3,
-  LSG_TILE_8x64 = 4,
+  LSG_TILE_16x116 = 0,
+  LSG_TILE_32x116 = 1,
+  LSG_TILE_8x232 = 2,
+  LSG_TILE_16x232 = 3,
+  LSG_TILE_32x232 = 4,
   LSG_TILE_COUNT = 5
 };
 
@@ -182,8 +184,9 @@ lsg_status lsg_set_tile(lsg_ctx* ctx, int tile);
 /*
  * Segments one scan (Sec. 2: meshing, normal estimation, Algorithm 1,
  * back-fill): decode -> mesh -> normals -> edge mask -> connected components
- * -> back-fill.  The workspace (ring order, union-find parents: 4*(2H + H*Ws)
- * bytes) is allocated in the context on first need.
+ * -> back-fill.  The workspace (ring order and sin/cos per ring, union-find
+ * parents and tile-local roots: 12*H + 6*H*Ws bytes) is allocated in the
+ * context on first need.
  */
 lsg_status lsg_segment(lsg_ctx* ctx, const lsg_scan* scan, const lsg_params* params,
                        const lsg_out* out, lsg_stream stream);
@@ -255,11 +258,11 @@ lsg_status lsg_get_error(lsg_ctx* ctx);
  * driver-wide locks) or a host framework that owns all device memory and
  * forbids side allocations.  The caller still allocates and owns the inputs
  * and outputs; the workspace is one fixed device array inside the library
- * (about 4.3 MB on every device that loads the library, held until the
+ * (about 6.3 MB on every device that loads the library, held until the
  * process exits).
  *
  *   scan, params, out  as for lsg_segment; uses the current CUDA device and
- *                      the 8x128 tile shape.  Outputs equal lsg_segment's.
+ *                      the default tile shape.  Outputs equal lsg_segment's.
  *   returns LSG_E_SHAPE when rings * ceil(cols/subsample) exceeds
  *   LSG_NOALLOC_MAX_VERTICES (nothing is launched), LSG_E_ARG / LSG_E_SHAPE
  *   as lsg_segment for bad arguments, LSG_E_CUDA if a launch fails.

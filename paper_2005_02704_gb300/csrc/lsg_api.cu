@@ -21,12 +21,12 @@ struct lsg_ctx {
   void* ws = nullptr;       // single-scan workspace
   size_t ws_bytes = 0;
   int32_t* d_err = nullptr; // sticky device error word
-  int tile = LSG_TILE_8x128;
+  int tile = LSG_TILE_16x116;
 };
 
 struct lsg_plan {
   lsg_ctx* ctx = nullptr;
-  int tile = LSG_TILE_8x128;
+  int tile = LSG_TILE_16x116;
   int n = 0;
   std::vector<ScanDesc> host_desc;  // tile fields filled per tile shape
   ScanDesc* d_desc = nullptr;
@@ -142,7 +142,7 @@ namespace {
 
 size_t scan_ws_bytes(int H, int Ws) {
   return align_up(sizeof(int32_t) * H, 256) + align_up(sizeof(float2) * H, 256) +
-         align_up(sizeof(int32_t) * (size_t)H * Ws, 256);
+         align_up(sizeof(int32_t) * (size_t)H * Ws, 256) + align_up(sizeof(uint16_t) * (size_t)H * Ws, 256);
 }
 
 void carve_ws(ScanDesc& d, char* base) {
@@ -151,6 +151,8 @@ void carve_ws(ScanDesc& d, char* base) {
   d.trig = reinterpret_cast<float2*>(base);
   base += align_up(sizeof(float2) * d.H, 256);
   d.parent = reinterpret_cast<int32_t*>(base);
+  base += align_up(sizeof(int32_t) * (size_t)d.H * d.Ws, 256);
+  d.lroot = reinterpret_cast<uint16_t*>(base);
 }
 
 lsg_status reserve(lsg_ctx* ctx, size_t need) {
@@ -253,7 +255,7 @@ lsg_status lsg_destroy(lsg_ctx* ctx) {
 
 lsg_status lsg_set_tile(lsg_ctx* ctx, int tile) {
   if (!ctx) return LSG_E_ARG;
-  if (tile == LSG_TILE_AUTO) tile = LSG_TILE_8x128;
+  if (tile == LSG_TILE_AUTO) tile = LSG_TILE_16x116;
   if (tile < 0 || tile >= LSG_TILE_COUNT) return LSG_E_ARG;
   ctx->tile = tile;
   return LSG_OK;
@@ -418,10 +420,10 @@ lsg_status lsg_batch_plan(lsg_ctx* ctx, int32_t n, const lsg_scan* scans, const 
     if (st != LSG_OK) return st;
     ws_total += scan_ws_bytes(scans[b].rings, Ws[b]);
   }
-  // the tile table is largest for the smallest tile (8 x 64 vertices)
+  // bound on the tile table over every tile shape (at least 8 rows x 116 columns)
   size_t tiles_max = 0;
   for (int b = 0; b < n; ++b)
-    tiles_max += (size_t)((scans[b].rings + 1) / 2 + 1) * ((Ws[b] + 63) / 64 + 1);
+    tiles_max += (size_t)(scans[b].rings / 8 + 1) * (Ws[b] / 116 + 1);
   const size_t bytes = ws_total + align_up(sizeof(ScanDesc) * n, 256) + sizeof(int32_t) * tiles_max;
   if (ctx->budget && ctx->used + bytes > ctx->budget) return LSG_E_BUDGET;
   DeviceGuard g(ctx->device);

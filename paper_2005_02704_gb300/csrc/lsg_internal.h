@@ -5,7 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/lsg.h"
+#include "lsg.h"  // include/ is on the include path
 
 namespace lsg {
 
@@ -26,6 +26,8 @@ struct ScanDesc {
   int32_t* order;       // [H]   sorted ring -> input row
   float2* trig;         // [H]   (sin, cos) of the sorted ring's elevation
   int32_t* parent;      // [H*Ws] union-find over scan-local vertex indices
+                        //        (only entries of tile-local roots are used)
+  uint16_t* lroot;      // [H*Ws] each vertex's tile-local root (tile-local index)
   // shape
   int32_t H, W, Ws, s, wrap;  // wrap already reduced to (wrap && Ws >= 3)
   int32_t tiles_r, tiles_c, tile0;

@@ -5,22 +5,31 @@
 // (or a batch of scans) is four launches:
 //
 //   k_prep     ring order by elevation (rank counting), sin/cos of the sorted
-//              elevations, segment counter reset.                 [Sec. 2 point model]
-//   k_tile     one CTA per tile of TR x TC mesh vertices: stage the tile and a
-//              halo (1 ring above, 2 below, 1 column left, 2 right) of x,y,z,r in
-//              shared memory, then mesh bits, normals, the homogeneity mask and a
-//              tile-local union-find, all in shared memory; writes the mesh byte,
-//              the normal and each vertex's tile-local root.   [Sec. 2 mesh, normals;
-//                                                              Algorithm 1 predicate]
-//   k_merge    joins tile-local components across tile borders (and the 360 deg
-//              seam) with a lock-free atomicMin union-find in global memory.
-//   k_flatten  label = smallest full-resolution index of the component
-//              (path to the root), back-fill of non-sampled points, segment
-//              count with warp-aggregated atomics.              [Algorithm 1; Sec. 2 end]
+//              elevations, segment counter reset.               [Sec. 2, point model]
+//   k_tile     one CTA per tile of TR rows x (29*NW) columns of mesh vertices.
+//              The CTA stages x,y,z,r of the tile plus a halo (one ring above,
+//              two below, one column left, two right) in shared memory.  Each
+//              warp then sweeps a strip of 32 columns (29 of them its own)
+//              down the rows, holding a three-row window in registers and
+//              taking the neighbouring columns from the adjacent lanes with
+//              warp shuffles: mesh bits and edge vectors of each row, the
+//              weighted normal of the row above, the homogeneity mask of the
+//              row above that.  Every edge vector and length is computed once
+//              and reused by both endpoints.  The tile's components follow:
+//              horizontal runs from a warp ballot, vertical joins with an
+//              atomicMin union-find in shared memory (only where a run meets a
+//              new run above), then joins across strips.  Writes the mesh byte,
+//              the normal, and each vertex's tile-local root (16 bits).
+//                                          [Sec. 2 mesh, normals; Algorithm 1]
+//   k_merge    joins tile-local components across tile borders and the 360 deg
+//              seam with a lock-free atomicMin union-find over the roots.
+//   k_flatten  label = smallest full-resolution index of the component,
+//              back-fill of non-sampled points, segment count with warp
+//              reductions.                                [Algorithm 1; Sec. 2 end]
 //
-// Labels are exact: the union-find always hooks the larger root under the
-// smaller, so every component's root is its smallest vertex index, whatever
-// the order in which threads run.
+// Labels are exact: every union hooks the larger root under the smaller, so
+// each component's root is its smallest vertex index whatever the thread
+// order, and a tile-local root is the smallest index of its tile component.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -28,20 +37,21 @@
 
 namespace lsg {
 
-constexpr int NT = 256;
-
 constexpr uint8_t B_R = LSG_BIT_R, B_D = LSG_BIT_D, B_G = LSG_BIT_G;
 constexpr uint8_t B_HR = LSG_BIT_HR, B_HD = LSG_BIT_HD, B_HG = LSG_BIT_HG;
 constexpr uint8_t B_VALID = LSG_BIT_VALID, B_HASN = LSG_BIT_HASN;
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int SO = 29;  // output columns per warp strip (lanes 1..29)
+constexpr uint16_t NO_ROOT = 0xFFFF;  // tile-local root of a vertex out of range
 
 TileShape tile_shape(int tile) {
   switch (tile) {
-    case LSG_TILE_4x256: return {4, 256};
-    case LSG_TILE_16x64: return {16, 64};
-    case LSG_TILE_2x512: return {2, 512};
-    case LSG_TILE_8x64: return {8, 64};
-    case LSG_TILE_8x128:
-    default: return {8, 128};
+    case LSG_TILE_32x116: return {32, 116};
+    case LSG_TILE_8x232: return {8, 232};
+    case LSG_TILE_16x232: return {16, 232};
+    case LSG_TILE_32x232: return {32, 232};
+    case LSG_TILE_16x116:
+    default: return {16, 116};
   }
 }
 
@@ -55,9 +65,38 @@ __device__ __forceinline__ bool in_range(float r, float rmin, float rmax) {
 // Depth-jump cut |r_p - r_q| > tau * min(r_p, r_q) in binary32, round to
 // nearest, never contracted into an FMA (the decision must be reproducible).
 __device__ __forceinline__ bool jump_cut(float rp, float rq, float tau) {
-  float d = fabsf(__fsub_rn(rp, rq));
-  float m = fminf(rp, rq);
-  return d > __fmul_rn(tau, m);
+  const float d = fabsf(__fsub_rn(rp, rq));
+  return d > __fmul_rn(tau, fminf(rp, rq));
+}
+
+// Length of a vector via the hardware reciprocal square root (about 2 ulp).
+__device__ __forceinline__ float vlen(float x, float y, float z) {
+  const float q = fmaf(x, x, fmaf(y, y, z * z));
+  return q > 0.f ? q * rsqrtf(q) : 0.f;
+}
+
+// One weighted triangle term of the normal sum (Sec. 2, normal estimation):
+// w (a x b) with w = 1 / (|a| + |b|), added only when the triangle exists.
+// Spokes of missing triangles may point at absent points, so their term is
+// dropped after the arithmetic instead of being multiplied by zero.
+__device__ __forceinline__ void tri_term(float ax, float ay, float az, float la, float bx, float by, float bz,
+                                         float lb, bool exists, float& sx, float& sy, float& sz) {
+  const float w = __frcp_rn(la + lb);
+  const float tx = w * (ay * bz - az * by);
+  const float ty = w * (az * bx - ax * bz);
+  const float tz = w * (ax * by - ay * bx);
+  sx += exists ? tx : 0.f;
+  sy += exists ? ty : 0.f;
+  sz += exists ? tz : 0.f;
+}
+
+// Homogeneity predicate of Algorithm 1 between two vertices' normals
+// (w = 1 when the vertex has a normal).
+__device__ __forceinline__ bool homog(const float4 u, const float4 v, bool angle_pred, float cos_t, float cx,
+                                      float cy, float cz) {
+  if (u.w == 0.f || v.w == 0.f) return false;
+  if (angle_pred) return fmaf(u.x, v.x, fmaf(u.y, v.y, u.z * v.z)) > cos_t;
+  return fabsf(u.x - v.x) < cx && fabsf(u.y - v.y) < cy && fabsf(u.z - v.z) < cz;
 }
 
 __device__ __forceinline__ const ScanDesc* tile_desc(const KArgs& a, int t, int& lt) {
@@ -88,11 +127,11 @@ __device__ void union_s(int* P, int a, int b, int limit, int32_t* err) {
     b = find_s(V, b, limit);
     if (a == b) return;
     if (a > b) {
-      int t = a;
+      const int t = a;
       a = b;
       b = t;
     }
-    int old = atomicMin(P + b, a);
+    const int old = atomicMin(P + b, a);
     if (old == b) return;
     b = old;
   }
@@ -110,17 +149,31 @@ __device__ __forceinline__ int find_g(const int32_t* P, int x, int limit) {
   return x;
 }
 
+// find with path halving: each visited node is re-pointed at its grandparent.
+// The store only shortens a path to an ancestor (P[x] <= x still holds), so it
+// is safe next to concurrent atomicMin links.
+__device__ __forceinline__ int find_halve(int32_t* P, int x, int limit) {
+  int p = __ldcg(P + x);
+  while (p != x && limit-- > 0) {
+    const int gp = __ldcg(P + p);
+    if (gp != p) __stcg(P + x, gp);
+    x = gp;
+    p = __ldcg(P + x);
+  }
+  return x;
+}
+
 __device__ void union_g(int32_t* P, int a, int b, int limit, int32_t* err) {
   for (int it = 0; it < limit; ++it) {
-    a = find_g(P, a, limit);
-    b = find_g(P, b, limit);
+    a = find_halve(P, a, limit);
+    b = find_halve(P, b, limit);
     if (a == b) return;
     if (a > b) {
-      int t = a;
+      const int t = a;
       a = b;
       b = t;
     }
-    int old = atomicMin(P + b, a);
+    const int old = atomicMin(P + b, a);
     if (old == b) return;
     b = old;
   }
@@ -130,21 +183,23 @@ __device__ void union_g(int32_t* P, int a, int b, int limit, int32_t* err) {
 // ---------------------------------------------------------------------------
 // k_prep: ring order (Sec. 2: rings counted from the topmost sensor down)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(NT) k_prep(const __grid_constant__ KArgs a) {
+constexpr int NT_PREP = 256;
+
+__global__ void __launch_bounds__(NT_PREP) k_prep(const __grid_constant__ KArgs a) {
   __shared__ float se[LSG_MAX_RINGS];
   const ScanDesc* d = a.scans ? a.scans + blockIdx.x : &a.one;
   const int H = d->H;
-  for (int k = threadIdx.x; k < H; k += NT) {
+  for (int k = threadIdx.x; k < H; k += NT_PREP) {
     se[k] = d->elev[k];
     d->order[k] = -1;
   }
   __syncthreads();
-  for (int k = threadIdx.x; k < H; k += NT) {
-    float e = se[k];
+  for (int k = threadIdx.x; k < H; k += NT_PREP) {
+    const float e = se[k];
     if (e != e) atomicOr(a.err, DERR_NAN_ELEV);
     int rank = 0;
     for (int m = 0; m < H; ++m) {
-      float em = se[m];
+      const float em = se[m];
       rank += (em > e) || (em == e && m < k);
     }
     if (rank < H) {
@@ -158,289 +213,421 @@ __global__ void __launch_bounds__(NT) k_prep(const __grid_constant__ KArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// tile geometry in shared memory
+// tile geometry
 // ---------------------------------------------------------------------------
-template <int TR, int TC>
+template <int TR, int NW>
 struct Geo {
-  static constexpr int HR = TR + 3, HC = TC + 3;  // halo: rows r0-1..r0+TR+1, cols c0-1..c0+TC+1
-  static constexpr int NR = TR + 1, NC = TC + 1;  // normals: rows r0..r0+TR, cols c0..c0+TC
-  static constexpr int NH = HR * HC, NN = NR * NC, NV = TR * TC;
+  static constexpr int NT = NW * 32;
+  static constexpr int TC = NW * SO;             // output columns of a tile
+  static constexpr int HR = TR + 3;              // staged rows  r0-1 .. r0+TR+1
+  static constexpr int HC = TC + 3;              // staged cols  c0-1 .. c0+TC+1
+  static constexpr int NV = TR * TC;
   static constexpr size_t off_hx = 0;
-  static constexpr size_t off_hn = off_hx + sizeof(float4) * NH;
-  static constexpr size_t off_lp = off_hn + sizeof(float4) * NN;
-  static constexpr size_t off_hm = off_lp + sizeof(int) * NV;
-  static constexpr size_t off_tb = off_hm + ((NH + 15) / 16) * 16;
-  static constexpr size_t bytes = off_tb + ((NV + 15) / 16) * 16;
+  static constexpr size_t off_lp = off_hx + sizeof(float4) * HR * HC;
+  static constexpr size_t off_tb = off_lp + sizeof(int) * NV;
+  static constexpr size_t off_tg = off_tb + ((NV + 15) / 16) * 16;
+  static constexpr size_t bytes = off_tg + sizeof(float2) * HC;
+  static constexpr size_t ccl_bytes = sizeof(int) * NV + ((NV + 15) / 16) * 16;
 };
 
-// Weighted normal of the vertex at halo position k (Sec. 2, normal
-// estimation).  Spokes in the paper's anticlockwise order
-// A=(i+1,j) B=(i+1,j+1) C=(i,j+1) D=(i-1,j) E=(i-1,j-1) F=(i,j-1); triangle
-// (p, q_k, q_k+1) counts when its three edges are mesh edges; its term is
-// w_k (V_k x V_k+1), w_k = 1/(|V_k| + |V_k+1|).  Returns (n, 1) or (0, 0).
-template <int HC>
-__device__ __forceinline__ float4 vertex_normal(const float4* __restrict__ hx,
-                                                const uint8_t* __restrict__ hm, int k,
-                                                float nsign) {
-  const uint8_t bp = hm[k];
-  if (!(bp & B_VALID)) return make_float4(0.f, 0.f, 0.f, 0.f);
-  const int kq[6] = {k + HC, k + HC + 1, k + 1, k - HC, k - HC - 1, k - 1};
-  const uint8_t bA = hm[kq[0]], bC = hm[kq[2]], bD = hm[kq[3]], bE = hm[kq[4]], bF = hm[kq[5]];
-  bool spoke[6] = {(bp & B_D) != 0, (bp & B_G) != 0, (bp & B_R) != 0,
-                   (bD & B_D) != 0, (bE & B_G) != 0, (bF & B_R) != 0};
-  bool rim[6] = {(bA & B_R) != 0, (bC & B_D) != 0, (bD & B_G) != 0,
-                 (bE & B_R) != 0, (bE & B_D) != 0, (bF & B_G) != 0};
-  const float4 p = hx[k];
-  float vx[6], vy[6], vz[6], vl[6];
-#pragma unroll
-  for (int q = 0; q < 6; ++q) {
-    if (spoke[q]) {
-      float4 o = hx[kq[q]];
-      vx[q] = o.x - p.x;
-      vy[q] = o.y - p.y;
-      vz[q] = o.z - p.z;
-      vl[q] = norm3df(vx[q], vy[q], vz[q]);
-    } else {
-      vx[q] = vy[q] = vz[q] = vl[q] = 0.f;
-    }
-  }
-  float sx = 0.f, sy = 0.f, sz = 0.f;
-  int ntri = 0;
-#pragma unroll
-  for (int q = 0; q < 6; ++q) {
-    const int q1 = (q + 1) % 6;
-    if (spoke[q] && spoke[q1] && rim[q]) {
-      const float w = 1.0f / (vl[q] + vl[q1]);
-      sx += w * (vy[q] * vz[q1] - vz[q] * vy[q1]);
-      sy += w * (vz[q] * vx[q1] - vx[q] * vz[q1]);
-      sz += w * (vx[q] * vy[q1] - vy[q] * vx[q1]);
-      ++ntri;
-    }
-  }
-  if (ntri == 0) return make_float4(0.f, 0.f, 0.f, 0.f);
-  const float inv = rnorm3df(sx, sy, sz);
-  if (!(inv > 0.f) || !isfinite(inv)) return make_float4(0.f, 0.f, 0.f, 0.f);
-  const float f = nsign * inv;
-  return make_float4(sx * f, sy * f, sz * f, 1.f);
+// Everything of a descriptor the tile kernels use, in registers.
+struct Loc {
+  int H, W, Ws, s, wrap, tiles_c;
+  int r0, c0, rn, cn;
+};
+
+__device__ __forceinline__ Loc make_loc(const ScanDesc* d, int lt, int TR, int TC) {
+  Loc L;
+  L.H = d->H;
+  L.W = d->W;
+  L.Ws = d->Ws;
+  L.s = d->s;
+  L.wrap = d->wrap;
+  L.tiles_c = d->tiles_c;
+  const int tr = lt / L.tiles_c, tc = lt - tr * L.tiles_c;
+  L.r0 = tr * TR;
+  L.c0 = tc * TC;
+  L.rn = min(TR, L.H - L.r0);
+  L.cn = min(TC, L.Ws - L.c0);
+  return L;
 }
 
-// Homogeneity predicate of Algorithm 1 between two vertices' normals.
-__device__ __forceinline__ bool homog(const float4 a, const float4 b, const ScanDesc* d) {
-  if (a.w == 0.f || b.w == 0.f) return false;
-  if (d->pred == LSG_PRED_ANGLE) return a.x * b.x + a.y * b.y + a.z * b.z > d->cos_t;
-  return fabsf(a.x - b.x) < d->comp_x && fabsf(a.y - b.y) < d->comp_y &&
-         fabsf(a.z - b.z) < d->comp_z;
-}
+// Tile components of the tile bytes tb[TR][TC] (mesh + homogeneity bits of
+// the tile's own vertices): horizontal runs from a ballot, vertical joins in a
+// shared-memory union-find, then joins across strips and the seam.  Writes
+// every vertex's tile-local root to lroot and marks each root in parent.
+template <int TR, int NW>
+__device__ __forceinline__ void tile_components(const Loc& L, const uint8_t* __restrict__ tb, int* lp,
+                                uint16_t* __restrict__ lroot, int32_t* __restrict__ parent,
+                                int32_t* err) {
+  using G = Geo<TR, NW>;
+  constexpr int TC = G::TC;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int lcw = w * SO + lane - 1;  // this lane's tile column
+  const bool act = lane >= 1 && lane <= SO && lcw < L.cn;
 
-// Tile-local components over the homogeneous edges that stay inside the tile,
-// then each vertex's root written as a scan-local vertex index into parent[].
-// tb[] holds the final mesh byte of each tile vertex.
-template <int TR, int TC>
-__device__ void local_components(const ScanDesc* d, int r0, int c0, int rn, int cn,
-                                 const uint8_t* tb, int* lp, int32_t* err) {
-  using G = Geo<TR, TC>;
-  const int tid = threadIdx.x;
-  const bool full_ring = d->wrap && c0 == 0 && cn == d->Ws;  // seam inside the tile
-  for (int k = tid; k < G::NV; k += NT) lp[k] = k;
-  __syncthreads();
-  for (int k = tid; k < G::NV; k += NT) {
-    const int lr = k / TC, lc = k - (k / TC) * TC;
-    if (lr >= rn || lc >= cn) continue;
-    const uint8_t bits = tb[k];
-    if (bits & B_HR) {
-      if (lc + 1 < cn) union_s(lp, k, k + 1, G::NV + 1, err);
-      else if (full_ring) union_s(lp, k, lr * TC, G::NV + 1, err);
+  // C1: each warp walks its strip row by row
+  uint8_t bprev = 0;
+  for (int lr = 0; lr < L.rn; ++lr) {
+    const uint8_t b = act ? tb[lr * TC + lcw] : 0;
+    const bool hr_in = act && lane < SO && lcw + 1 < L.cn && (b & B_HR);
+    const unsigned B = __ballot_sync(FULL, hr_in);
+    const unsigned brk = ~B & ((1u << lane) - 1u);  // lanes left of me whose R edge breaks the run
+    const int start = 32 - __clz(brk);              // first lane of my run (>= 1)
+    const int v = lr * TC + lcw;
+    if (act) lp[v] = lr * TC + (w * SO + start - 1);
+    __syncwarp();
+    if (act && lr > 0) {
+      const uint8_t bu = bprev;
+      const uint8_t bul = lane >= 2 ? tb[(lr - 1) * TC + lcw - 1] : 0;
+      const uint8_t bl = lane >= 2 ? tb[lr * TC + lcw - 1] : 0;
+      // D edge (lr-1, c) - (lr, c); implied when the left lane's D edge and
+      // both rows' R edges already join the same vertices
+      if (bu & B_HD) {
+        const bool implied = (bul & B_HD) && (bul & B_HR) && (bl & B_HR);
+        if (!implied) union_s(lp, v, v - TC, G::NV + 1, err);
+      }
+      // G edge (lr-1, c-1) - (lr, c)
+      if (bul & B_HG) {
+        const bool implied = (bul & B_HD) && (bl & B_HR);
+        if (!implied) union_s(lp, v, v - TC - 1, G::NV + 1, err);
+      }
     }
-    if ((bits & B_HD) && lr + 1 < rn) union_s(lp, k, k + TC, G::NV + 1, err);
-    if ((bits & B_HG) && lr + 1 < rn) {
-      if (lc + 1 < cn) union_s(lp, k, k + TC + 1, G::NV + 1, err);
-      else if (full_ring) union_s(lp, k, (lr + 1) * TC, G::NV + 1, err);
-    }
+    __syncwarp();
+    bprev = b;
   }
   __syncthreads();
-  for (int k = tid; k < G::NV; k += NT) {
-    const int lr = k / TC, lc = k - (k / TC) * TC;
-    if (lr >= rn || lc >= cn) continue;
-    const int root = find_s(lp, k, G::NV + 1);
-    const int rr = root / TC, rc = root - (root / TC) * TC;
-    d->parent[(size_t)(r0 + lr) * d->Ws + (c0 + lc)] = (r0 + rr) * d->Ws + (c0 + rc);
+
+  // C2: edges across strip borders, and the seam of a tile spanning the ring
+  const bool full_ring = L.wrap && L.c0 == 0 && L.cn == L.Ws;
+  for (int idx = threadIdx.x; idx < L.rn * NW; idx += G::NT) {
+    const int lr = idx / NW, b = idx - (idx / NW) * NW;
+    int ac = -1, bc = -1;
+    if (b < NW - 1) {
+      ac = b * SO + SO - 1;
+      bc = ac + 1;
+      if (bc >= L.cn) ac = -1;
+    }
+    if (b == NW - 1 && full_ring) {
+      ac = L.cn - 1;
+      bc = 0;
+    }
+    if (ac < 0) continue;
+    const uint8_t bits = tb[lr * TC + ac];
+    if (bits & B_HR) union_s(lp, lr * TC + ac, lr * TC + bc, G::NV + 1, err);
+    if ((bits & B_HG) && lr + 1 < L.rn) union_s(lp, lr * TC + ac, (lr + 1) * TC + bc, G::NV + 1, err);
+  }
+  __syncthreads();
+
+  // C3: roots (vertices out of range: 0xFFFF)
+  for (int lr = w; lr < L.rn; lr += NW) {
+    for (int lc = lane; lc < L.cn; lc += 32) {
+      const int v = lr * TC + lc;
+      const size_t gv = (size_t)(L.r0 + lr) * L.Ws + (L.c0 + lc);
+      if (!(tb[v] & B_VALID)) {
+        lroot[gv] = NO_ROOT;
+        continue;
+      }
+      const int r = find_s(lp, v, G::NV + 1);
+      lroot[gv] = (uint16_t)r;
+      if (r == v) parent[gv] = (int32_t)gv;
+    }
   }
 }
 
 // ---------------------------------------------------------------------------
-// k_tile: decode + mesh + normals + edge mask + tile-local components
+// k_tile: decode + mesh + normals + edge mask + tile components
 // ---------------------------------------------------------------------------
-template <int TR, int TC>
-__global__ void __launch_bounds__(NT) k_tile(const __grid_constant__ KArgs a) {
-  using G = Geo<TR, TC>;
+template <int TR, int NW>
+__global__ void __launch_bounds__(NW * 32) k_tile(const __grid_constant__ KArgs a) {
+  using G = Geo<TR, NW>;
+  constexpr int TC = G::TC, HC = G::HC, HR = G::HR;
   extern __shared__ __align__(16) unsigned char smem[];
   float4* hx = reinterpret_cast<float4*>(smem + G::off_hx);
-  float4* hn = reinterpret_cast<float4*>(smem + G::off_hn);
   int* lp = reinterpret_cast<int*>(smem + G::off_lp);
-  uint8_t* hm = smem + G::off_hm;
   uint8_t* tb = smem + G::off_tb;
-  const int tid = threadIdx.x;
+  float2* tg = reinterpret_cast<float2*>(smem + G::off_tg);
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
 
   for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
     int lt;
     const ScanDesc* d = tile_desc(a, t, lt);
-    const int H = d->H, W = d->W, Ws = d->Ws, s = d->s;
-    const int tr = lt / d->tiles_c, tc = lt - (lt / d->tiles_c) * d->tiles_c;
-    const int r0 = tr * TR, c0 = tc * TC;
-    const int rn = min(TR, H - r0), cn = min(TC, Ws - c0);
-    const float rmin = d->r_min, rmax = d->r_max;
+    const Loc L = make_loc(d, lt, TR, TC);
+    const float4* __restrict__ xyzr = d->xyzr;
+    const float* __restrict__ range = d->range;
+    const int32_t* __restrict__ order = d->order;
+    const float rmin = d->r_min, rmax = d->r_max, jh = d->jump_h, jv = d->jump_v;
 
-    // 1. stage x, y, z, r of the tile and its halo (absent positions: r = -1)
-    for (int k = tid; k < G::NH; k += NT) {
-      const int hr = k / G::HC, hc = k - (k / G::HC) * G::HC;
-      const int i = r0 - 1 + hr;
-      int j = c0 - 1 + hc;
-      float4 v = make_float4(0.f, 0.f, 0.f, -1.f);
-      if (d->wrap) j = ((j % Ws) + Ws) % Ws;
-      if (i >= 0 && i < H && j >= 0 && j < Ws) {
-        const int row = d->order[i];
-        if ((unsigned)row < (unsigned)H) {
-          const size_t o = (size_t)row * W + (size_t)j * s;
-          if (d->xyzr) {
-            v = __ldg(d->xyzr + o);
-          } else {
-            const float r = __ldg(d->range + o);
-            const float2 tg = d->trig[i];
-            float sp, cp;
-            sincosf(fmaf((float)(j * s), d->daz, d->az0), &sp, &cp);
-            const float rc = r * tg.y;
-            v = make_float4(rc * cp, rc * sp, r * tg.x, r);
+    // 1. stage x, y, z, r of the tile and its halo (absent positions r = -1)
+    if (!xyzr) {
+      for (int hc = tid; hc < HC; hc += G::NT) {
+        int j = L.c0 - 1 + hc;
+        if (L.wrap) j = ((j % L.Ws) + L.Ws) % L.Ws;
+        float sp = 0.f, cp = 1.f;
+        sincosf(fmaf((float)(j * L.s), d->daz, d->az0), &sp, &cp);
+        tg[hc] = make_float2(sp, cp);
+      }
+      __syncthreads();
+    }
+    // x,y,z,r input: asynchronous 16-byte copies (cp.async), all of a
+    // thread's copies in flight at once; range input is decoded on the way.
+    for (int k = tid; k < HR * HC; k += G::NT) {
+      const int hr = k / HC, hc = k - (k / HC) * HC;
+      const int i = L.r0 - 1 + hr;
+      int j = L.c0 - 1 + hc;
+      if (L.wrap) {
+        if (j < 0) j += L.Ws;
+        else if (j >= L.Ws) j -= L.Ws;
+        if (j >= L.Ws) j %= L.Ws;
+      }
+      bool present = false;
+      size_t o = 0;
+      if (i >= 0 && i < L.H && j >= 0 && j < L.Ws) {
+        const int row = order[i];
+        if ((unsigned)row < (unsigned)L.H) {
+          o = (size_t)row * L.W + (size_t)j * L.s;
+          present = true;
+        }
+      }
+      if (!present) {
+        hx[k] = make_float4(0.f, 0.f, 0.f, -1.f);
+      } else if (xyzr) {
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(hx + k);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(xyzr + o) : "memory");
+      } else {
+        const float r = __ldg(range + o);
+        const float2 te = d->trig[i];
+        const float2 ta = tg[hc];
+        const float rc = r * te.y;
+        hx[k] = make_float4(rc * ta.y, rc * ta.x, r * te.x, r);
+      }
+    }
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+    __syncthreads();
+
+    // 2. the sweep: warp w owns staged columns w*29 .. w*29+31 (lanes), of
+    //    which lanes 1..29 are its output columns.  At step hr the warp reads
+    //    staged row hr (scan row r0-1+hr) and completes: the R edge of that
+    //    row, the D and G edges of the row above, the normal of the row above
+    //    that (Sec. 2, normal estimation) and the mask of the row above that
+    //    (Algorithm 1 predicate).
+    {
+      const int col = w * SO + lane;  // staged column
+      const int lc = col - 1;         // tile column
+      const bool out_col = lane >= 1 && lane <= SO && lc < L.cn;
+      const float nsign = d->nsign, cos_t = d->cos_t;
+      const float cx = d->comp_x, cy = d->comp_y, cz = d->comp_z;
+      const bool angle_pred = d->pred == LSG_PRED_ANGLE;
+      uint8_t* __restrict__ mb_out = d->mb;
+      float* __restrict__ nrm_out = d->nrm;
+
+      float4 Pp = make_float4(0.f, 0.f, 0.f, -1.f);           // row k-1
+      float eRx_p = 0.f, eRy_p = 0.f, eRz_p = 0.f, LR_p = 0.f;  // R edge of row k-1
+      float eDx_pp = 0.f, eDy_pp = 0.f, eDz_pp = 0.f, LD_pp = 0.f;  // D edge of row k-2
+      float eGx_ppL = 0.f, eGy_ppL = 0.f, eGz_ppL = 0.f, LG_ppL = 0.f;  // G edge of row k-2, left lane
+      uint32_t m_pp = 0, m_p = 0;                                // mesh bits of rows k-2, k-1
+      float4 n_pp = make_float4(0.f, 0.f, 0.f, 0.f);             // normal of row k-2
+
+      for (int hr = 0; hr < HR; ++hr) {
+        const float4 P = hx[hr * HC + col];
+        float4 Pr;
+        Pr.x = __shfl_down_sync(FULL, P.x, 1);
+        Pr.y = __shfl_down_sync(FULL, P.y, 1);
+        Pr.z = __shfl_down_sync(FULL, P.z, 1);
+        Pr.w = __shfl_down_sync(FULL, P.w, 1);
+        const bool vP = in_range(P.w, rmin, rmax);
+        const bool vPr = lane < 31 && in_range(Pr.w, rmin, rmax);
+        // R edge of row k
+        const bool Rk = vP && vPr && !jump_cut(P.w, Pr.w, jh);
+        const float eRx = Pr.x - P.x, eRy = Pr.y - P.y, eRz = Pr.z - P.z;
+        const float LR = vlen(eRx, eRy, eRz);
+        // D and G edges of row k-1
+        const bool vPp = in_range(Pp.w, rmin, rmax);
+        const bool Dk1 = vPp && vP && !jump_cut(Pp.w, P.w, jv);
+        const bool Gk1 = vPp && vPr && !jump_cut(Pp.w, Pr.w, jv);
+        const float eDx = P.x - Pp.x, eDy = P.y - Pp.y, eDz = P.z - Pp.z;
+        const float eGx = Pr.x - Pp.x, eGy = Pr.y - Pp.y, eGz = Pr.z - Pp.z;
+        const float LD = vlen(eDx, eDy, eDz), LG = vlen(eGx, eGy, eGz);
+        m_p |= (Dk1 ? B_D : 0u) | (Gk1 ? B_G : 0u);
+        const uint32_t m_k = (Rk ? B_R : 0u) | (vP ? B_VALID : 0u);
+        // neighbours' mesh bits (byte 0: row k-2, byte 1: row k-1, byte 2: row k)
+        const uint32_t word = m_pp | (m_p << 8) | (m_k << 16);
+        const uint32_t up = __shfl_up_sync(FULL, word, 1);
+        const uint32_t dn = __shfl_down_sync(FULL, word, 1);
+        const float eRxL = __shfl_up_sync(FULL, eRx_p, 1);
+        const float eRyL = __shfl_up_sync(FULL, eRy_p, 1);
+        const float eRzL = __shfl_up_sync(FULL, eRz_p, 1);
+        const float LRL = __shfl_up_sync(FULL, LR_p, 1);
+
+        // normal of row k-1, vertex p (spokes in the paper's order A..F):
+        // A = eD, B = eG, C = eR(k-1), D = -eD(k-2), E = -eG(k-2, left),
+        // F = -eR(k-1, left); triangle (p, q, q') counts when its 3 edges exist
+        float4 n_p = make_float4(0.f, 0.f, 0.f, 0.f);
+        {
+          const uint32_t upp = up & 0xff, upl = (up >> 8) & 0xff, dnl = (dn >> 8) & 0xff;
+          const bool sA = Dk1, sB = Gk1, sC = (m_p & B_R) != 0, sD = (m_pp & B_D) != 0;
+          const bool sE = (upp & B_G) != 0, sF = (upl & B_R) != 0;
+          float sx = 0.f, sy = 0.f, sz = 0.f;
+          tri_term(eDx, eDy, eDz, LD, eGx, eGy, eGz, LG, sA && sB && Rk, sx, sy, sz);
+          tri_term(eGx, eGy, eGz, LG, eRx_p, eRy_p, eRz_p, LR_p, sB && sC && (dnl & B_D), sx, sy, sz);
+          tri_term(eRx_p, eRy_p, eRz_p, LR_p, -eDx_pp, -eDy_pp, -eDz_pp, LD_pp, sC && sD && (m_pp & B_G), sx, sy,
+                   sz);
+          tri_term(-eDx_pp, -eDy_pp, -eDz_pp, LD_pp, -eGx_ppL, -eGy_ppL, -eGz_ppL, LG_ppL,
+                   sD && sE && (upp & B_R), sx, sy, sz);
+          tri_term(-eGx_ppL, -eGy_ppL, -eGz_ppL, LG_ppL, -eRxL, -eRyL, -eRzL, LRL, sE && sF && (upp & B_D), sx, sy,
+                   sz);
+          tri_term(-eRxL, -eRyL, -eRzL, LRL, eDx, eDy, eDz, LD, sF && sA && (upl & B_G), sx, sy, sz);
+          const float q2 = fmaf(sx, sx, fmaf(sy, sy, sz * sz));
+          // q2 > 0 only when some triangle counted (absent terms are exact zeros)
+          if ((m_p & B_VALID) && q2 > 0.f && q2 < 3.0e38f) {
+            const float f = nsign * rsqrtf(q2);
+            n_p = make_float4(sx * f, sy * f, sz * f, 1.f);
           }
         }
-      }
-      hx[k] = v;
-    }
-    __syncthreads();
 
-    // 2. mesh bits on the halo (Sec. 2, mesh construction): R, D, G joins
-    //    between points in range and not across a depth jump
-    for (int k = tid; k < G::NH; k += NT) {
-      const int hr = k / G::HC, hc = k - (k / G::HC) * G::HC;
-      const float rp = hx[k].w;
-      uint8_t bits = 0;
-      if (in_range(rp, rmin, rmax)) {
-        bits = B_VALID;
-        if (hc + 1 < G::HC) {
-          const float rq = hx[k + 1].w;
-          if (in_range(rq, rmin, rmax) && !jump_cut(rp, rq, d->jump_h)) bits |= B_R;
-        }
-        if (hr + 1 < G::HR) {
-          const float rq = hx[k + G::HC].w;
-          if (in_range(rq, rmin, rmax) && !jump_cut(rp, rq, d->jump_v)) bits |= B_D;
-          if (hc + 1 < G::HC) {
-            const float rg = hx[k + G::HC + 1].w;
-            if (in_range(rg, rmin, rmax) && !jump_cut(rp, rg, d->jump_v)) bits |= B_G;
+        // homogeneity mask and outputs of row k-2
+        if (hr >= 3) {
+          const float4 nr_pp = make_float4(__shfl_down_sync(FULL, n_pp.x, 1), __shfl_down_sync(FULL, n_pp.y, 1),
+                                           __shfl_down_sync(FULL, n_pp.z, 1), __shfl_down_sync(FULL, n_pp.w, 1));
+          const float4 nr_p = make_float4(__shfl_down_sync(FULL, n_p.x, 1), __shfl_down_sync(FULL, n_p.y, 1),
+                                          __shfl_down_sync(FULL, n_p.z, 1), __shfl_down_sync(FULL, n_p.w, 1));
+          const int lr = hr - 3;
+          if (out_col && lr < L.rn) {
+            uint32_t bits = m_pp;
+            if (n_pp.w != 0.f) bits |= B_HASN;
+            if ((m_pp & B_R) && homog(n_pp, nr_pp, angle_pred, cos_t, cx, cy, cz)) bits |= B_HR;
+            if ((m_pp & B_D) && homog(n_pp, n_p, angle_pred, cos_t, cx, cy, cz)) bits |= B_HD;
+            if ((m_pp & B_G) && homog(n_pp, nr_p, angle_pred, cos_t, cx, cy, cz)) bits |= B_HG;
+            const size_t v = (size_t)(L.r0 + lr) * L.Ws + (L.c0 + lc);
+            mb_out[v] = (uint8_t)bits;
+            nrm_out[3 * v + 0] = n_pp.x;
+            nrm_out[3 * v + 1] = n_pp.y;
+            nrm_out[3 * v + 2] = n_pp.z;
+            tb[lr * TC + lc] = (uint8_t)bits;
           }
         }
+
+        // rotate the window
+        const float gxL = __shfl_up_sync(FULL, eGx, 1), gyL = __shfl_up_sync(FULL, eGy, 1);
+        const float gzL = __shfl_up_sync(FULL, eGz, 1), gLL = __shfl_up_sync(FULL, LG, 1);
+        m_pp = m_p;
+        m_p = m_k;
+        eDx_pp = eDx;
+        eDy_pp = eDy;
+        eDz_pp = eDz;
+        LD_pp = LD;
+        eGx_ppL = gxL;
+        eGy_ppL = gyL;
+        eGz_ppL = gzL;
+        LG_ppL = gLL;
+        eRx_p = eRx;
+        eRy_p = eRy;
+        eRz_p = eRz;
+        LR_p = LR;
+        n_pp = n_p;
+        Pp = P;
       }
-      hm[k] = bits;
     }
     __syncthreads();
 
-    // 3. normals of the tile plus one ring below and one column right
-    for (int k = tid; k < G::NN; k += NT) {
-      const int nr = k / G::NC, nc = k - (k / G::NC) * G::NC;
-      hn[k] = vertex_normal<G::HC>(hx, hm, (nr + 1) * G::HC + (nc + 1), d->nsign);
-    }
-    __syncthreads();
-
-    // 4. homogeneity mask of the tile's R, D, G edges; write mesh byte + normal
-    for (int k = tid; k < G::NV; k += NT) {
-      const int lr = k / TC, lc = k - (k / TC) * TC;
-      uint8_t bits = 0;
-      if (lr < rn && lc < cn) {
-        bits = hm[(lr + 1) * G::HC + (lc + 1)];
-        const float4 n = hn[lr * G::NC + lc];
-        if (n.w != 0.f) bits |= B_HASN;
-        if ((bits & B_R) && homog(n, hn[lr * G::NC + lc + 1], d)) bits |= B_HR;
-        if ((bits & B_D) && homog(n, hn[(lr + 1) * G::NC + lc], d)) bits |= B_HD;
-        if ((bits & B_G) && homog(n, hn[(lr + 1) * G::NC + lc + 1], d)) bits |= B_HG;
-        const size_t v = (size_t)(r0 + lr) * Ws + (c0 + lc);
-        d->mb[v] = bits;
-        float* o = d->nrm + 3 * v;
-        o[0] = n.x;
-        o[1] = n.y;
-        o[2] = n.z;
-      }
-      tb[k] = bits;
-    }
-    __syncthreads();
-
-    // 5. tile-local components (Algorithm 1 restricted to the tile)
-    local_components<TR, TC>(d, r0, c0, rn, cn, tb, lp, a.err);
+    // 3. tile components (Algorithm 1 restricted to the tile)
+    tile_components<TR, NW>(L, tb, lp, d->lroot, d->parent, a.err);
     __syncthreads();
   }
 }
 
 // ---------------------------------------------------------------------------
-// k_tile_ccl: tile-local components from a given mesh byte array
+// k_tile_ccl: tile components of a given mesh byte array
 // ---------------------------------------------------------------------------
-template <int TR, int TC>
-__global__ void __launch_bounds__(NT) k_tile_ccl(const __grid_constant__ KArgs a) {
-  using G = Geo<TR, TC>;
-  __shared__ int lp[G::NV];
-  __shared__ uint8_t tb[G::NV];
-  const int tid = threadIdx.x;
+template <int TR, int NW>
+__global__ void __launch_bounds__(NW * 32) k_tile_ccl(const __grid_constant__ KArgs a) {
+  using G = Geo<TR, NW>;
+  constexpr int TC = G::TC;
+  extern __shared__ __align__(16) unsigned char smem[];
+  int* lp = reinterpret_cast<int*>(smem);
+  uint8_t* tb = smem + sizeof(int) * G::NV;
   for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
     int lt;
     const ScanDesc* d = tile_desc(a, t, lt);
-    const int tr = lt / d->tiles_c, tc = lt - (lt / d->tiles_c) * d->tiles_c;
-    const int r0 = tr * TR, c0 = tc * TC;
-    const int rn = min(TR, d->H - r0), cn = min(TC, d->Ws - c0);
-    for (int k = tid; k < G::NV; k += NT) {
+    const Loc L = make_loc(d, lt, TR, TC);
+    for (int k = threadIdx.x; k < G::NV; k += G::NT) {
       const int lr = k / TC, lc = k - (k / TC) * TC;
-      tb[k] = (lr < rn && lc < cn) ? d->mb[(size_t)(r0 + lr) * d->Ws + (c0 + lc)] : 0;
+      tb[k] = (lr < L.rn && lc < L.cn) ? d->mb[(size_t)(L.r0 + lr) * L.Ws + (L.c0 + lc)] : 0;
     }
     __syncthreads();
-    local_components<TR, TC>(d, r0, c0, rn, cn, tb, lp, a.err);
+    tile_components<TR, NW>(L, tb, lp, d->lroot, d->parent, a.err);
     __syncthreads();
   }
+}
+
+// ---------------------------------------------------------------------------
+// global roots
+// ---------------------------------------------------------------------------
+// Scan-local index of the tile-local root of vertex (i, j).
+template <int TR, int TC>
+__device__ __forceinline__ int tile_root(const uint16_t* __restrict__ lroot, int Ws, int i, int j) {
+  const int r = lroot[(size_t)i * Ws + j];
+  const int rr = r / TC, rc = r - (r / TC) * TC;
+  return ((i / TR) * TR + rr) * Ws + (j / TC) * TC + rc;
 }
 
 // ---------------------------------------------------------------------------
 // k_merge: join components across tile borders and the 360 deg seam
 // ---------------------------------------------------------------------------
-template <int TR, int TC>
-__global__ void __launch_bounds__(NT) k_merge(const __grid_constant__ KArgs a) {
-  const int tid = threadIdx.x;
+constexpr int NT_MERGE = 128;
+
+template <int TR, int NW>
+__global__ void __launch_bounds__(NT_MERGE) k_merge(const __grid_constant__ KArgs a) {
+  constexpr int TC = NW * SO;
   for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
     int lt;
     const ScanDesc* d = tile_desc(a, t, lt);
-    const int Ws = d->Ws;
-    const int tr = lt / d->tiles_c, tc = lt - (lt / d->tiles_c) * d->tiles_c;
-    const int r0 = tr * TR, c0 = tc * TC;
-    const int rn = min(TR, d->H - r0), cn = min(TC, Ws - c0);
-    const int limit = d->H * Ws + 1;
+    const Loc L = make_loc(d, lt, TR, TC);
+    const uint8_t* __restrict__ mb = d->mb;
+    const uint16_t* __restrict__ lroot = d->lroot;
+    int32_t* parent = d->parent;
+    const int limit = L.H * L.Ws + 1;
+    const bool full_ring = L.wrap && L.c0 == 0 && L.cn == L.Ws;
     // border vertices: the last row of the tile, then the last column above it
-    const int nb = cn + rn - 1;
-    for (int k = tid; k < nb; k += NT) {
+    const int nb = L.cn + L.rn - 1;
+    for (int k = threadIdx.x; k < nb; k += NT_MERGE) {
       int lr, lc;
-      if (k < cn) {
-        lr = rn - 1;
+      if (k < L.cn) {
+        lr = L.rn - 1;
         lc = k;
       } else {
-        lr = k - cn;
-        lc = cn - 1;
+        lr = k - L.cn;
+        lc = L.cn - 1;
       }
-      const int i = r0 + lr, j = c0 + lc;
-      const int v = i * Ws + j;
-      const uint8_t bits = d->mb[v];
+      const int i = L.r0 + lr, j = L.c0 + lc;
+      const uint8_t bits = mb[(size_t)i * L.Ws + j];
       if (!(bits & (B_HR | B_HD | B_HG))) continue;
-      // bits that point off the grid (possible in a caller-given mask) are ignored
-      const bool has_right = (j + 1 < Ws) || d->wrap;
-      const bool has_down = i + 1 < d->H;
-      const int jn = (j + 1 == Ws) ? 0 : j + 1;
-      const bool jn_in = jn >= c0 && jn < c0 + cn;
-      const bool in_next_row = (i + 1) < r0 + rn;
-      if ((bits & B_HR) && has_right && !jn_in) union_g(d->parent, v, i * Ws + jn, limit, a.err);
-      if ((bits & B_HD) && has_down && !in_next_row) union_g(d->parent, v, (i + 1) * Ws + j, limit, a.err);
-      if ((bits & B_HG) && has_down && has_right && !(in_next_row && jn_in))
-        union_g(d->parent, v, (i + 1) * Ws + jn, limit, a.err);
+      // bits pointing off the grid (possible in a caller-given mask) are ignored
+      const bool has_right = (j + 1 < L.Ws) || L.wrap;
+      const bool has_down = i + 1 < L.H;
+      const int jn = (j + 1 == L.Ws) ? 0 : j + 1;
+      const bool jn_in = (lc + 1 < L.cn) || full_ring;
+      const bool down_in = lr + 1 < L.rn;
+      const bool hr_out = (bits & B_HR) && has_right && !jn_in;
+      const bool hd_out = (bits & B_HD) && has_down && !down_in;
+      const bool hg_out = (bits & B_HG) && has_down && has_right && !(down_in && jn_in);
+      if (!(hr_out || hd_out || hg_out)) continue;
+      if (lroot[(size_t)i * L.Ws + j] == NO_ROOT) continue;
+      // along the bottom border, a D edge whose two tile roots equal those of
+      // the left neighbour's D edge adds nothing
+      if (hd_out && !hr_out && !hg_out && k > 0 && k < L.cn) {
+        const uint8_t bl = mb[(size_t)i * L.Ws + j - 1];
+        if ((bl & B_HD) && lroot[(size_t)i * L.Ws + j - 1] == lroot[(size_t)i * L.Ws + j] &&
+            lroot[(size_t)(i + 1) * L.Ws + j - 1] == lroot[(size_t)(i + 1) * L.Ws + j])
+          continue;
+      }
+      const int rp = tile_root<TR, TC>(lroot, L.Ws, i, j);
+      if (hr_out && lroot[(size_t)i * L.Ws + jn] != NO_ROOT)
+        union_g(parent, rp, tile_root<TR, TC>(lroot, L.Ws, i, jn), limit, a.err);
+      if (hd_out && lroot[(size_t)(i + 1) * L.Ws + j] != NO_ROOT)
+        union_g(parent, rp, tile_root<TR, TC>(lroot, L.Ws, i + 1, j), limit, a.err);
+      if (hg_out && lroot[(size_t)(i + 1) * L.Ws + jn] != NO_ROOT)
+        union_g(parent, rp, tile_root<TR, TC>(lroot, L.Ws, i + 1, jn), limit, a.err);
     }
   }
 }
@@ -448,146 +635,197 @@ __global__ void __launch_bounds__(NT) k_merge(const __grid_constant__ KArgs a) {
 // ---------------------------------------------------------------------------
 // k_flatten: labels, back-fill, segment count
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int32_t vertex_label(const ScanDesc* d, int i, int j, int limit) {
-  const int v = i * d->Ws + j;
-  if (!(d->mb[v] & B_VALID)) return -1;
-  const int g = find_g(d->parent, v, limit);
-  const int gi = g / d->Ws, gj = g - (g / d->Ws) * d->Ws;
-  return gi * d->W + gj * d->s;
+constexpr int NT_FLAT = 256;
+
+// Root of a chain in the (now read-only) global union-find: cached loads.
+__device__ __forceinline__ int find_ro(const int32_t* __restrict__ P, int x, int limit) {
+  int p = __ldg(P + x);
+  while (p != x && limit-- > 0) {
+    x = p;
+    p = __ldg(P + x);
+  }
+  return x;
 }
 
+// Label of any vertex of the scan (used for the back-fill neighbour that lies
+// in the next tile).
 template <int TR, int TC>
-__global__ void __launch_bounds__(NT) k_flatten(const __grid_constant__ KArgs a) {
-  const int tid = threadIdx.x;
+__device__ __forceinline__ int32_t vertex_label_global(const uint16_t* __restrict__ lroot,
+                                                       const int32_t* __restrict__ parent, int Ws, int W,
+                                                       int s, int i, int j, int limit) {
+  if (lroot[(size_t)i * Ws + j] == NO_ROOT) return -1;
+  const int g = find_ro(parent, tile_root<TR, TC>(lroot, Ws, i, j), limit);
+  const int gi = g / Ws, gj = g - gi * Ws;
+  return gi * W + gj * s;
+}
+
+// Label of a point between sampled columns (Sec. 2, last paragraph): the
+// nearer of the two bracketing sampled columns on its ring, ties to the
+// earlier, the other when the nearer is unlabelled.
+__device__ __forceinline__ int32_t backfill(int32_t lo, int dlo, int32_t hi, int dhi, bool have_hi) {
+  int32_t first = lo, second = have_hi ? hi : -1;
+  if (have_hi && dhi < dlo) {
+    first = hi;
+    second = lo;
+  }
+  return first != -1 ? first : second;
+}
+
+// Per tile: (1) stage the tile's 16-bit local roots in shared memory,
+// (2) resolve every local root once to its global root and label (and count
+// the global roots), (3) write every point's label, back-filling the points
+// between sampled columns.  Loops are two-dimensional (warps over rows,
+// lanes over columns): no integer division per point.
+template <int TR, int NW>
+__global__ void __launch_bounds__(NT_FLAT) k_flatten(const __grid_constant__ KArgs a) {
+  constexpr int TC = NW * SO, NV = TR * TC, NWF = NT_FLAT / 32;
+  __shared__ uint16_t lr_s[NV];
+  __shared__ int32_t lab_s[NV];
+  const int tid = threadIdx.x, lane = tid & 31, wf = tid >> 5;
   for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
     int lt;
     const ScanDesc* d = tile_desc(a, t, lt);
-    const int W = d->W, Ws = d->Ws, s = d->s;
-    const int tr = lt / d->tiles_c, tc = lt - (lt / d->tiles_c) * d->tiles_c;
-    const int r0 = tr * TR, c0 = tc * TC;
-    const int rn = min(TR, d->H - r0), cn = min(TC, Ws - c0);
-    const int cbeg = c0 * s, cend = min((c0 + cn) * s, W);
-    const int ncols = cend - cbeg;
-    const int limit = d->H * Ws + 1;
-    const int npts = rn * ncols;
-    // whole warps iterate together so the warp-wide count reduction is safe
-    const int nround = (npts + NT - 1) / NT;
-    for (int rnd = 0; rnd < nround; ++rnd) {
-      const int k = rnd * NT + tid;
-      int root = 0;
-      if (k < npts) {
-        const int lr = k / ncols, cc = k - (k / ncols) * ncols;
-        const int i = r0 + lr, c = cbeg + cc;
-        const int j = c / s, rem = c - j * s;
-        int32_t lab;
-        if (rem == 0) {
-          const int v = i * Ws + j;
-          if (d->mb[v] & B_VALID) {
-            const int g = find_g(d->parent, v, limit);
-            root = (g == v);
-            const int gi = g / Ws, gj = g - gi * Ws;
-            lab = gi * W + gj * s;
-          } else {
-            lab = -1;
+    const Loc L = make_loc(d, lt, TR, TC);
+    const int W = L.W, Ws = L.Ws, s = L.s;
+    const uint16_t* __restrict__ lroot = d->lroot;
+    const int32_t* __restrict__ parent = d->parent;
+    int32_t* __restrict__ labels = d->labels;
+    const int limit = L.H * Ws + 1;
+    for (int lr = wf; lr < L.rn; lr += NWF) {
+      const uint16_t* src = lroot + (size_t)(L.r0 + lr) * Ws + L.c0;
+#pragma unroll 4
+      for (int lc = lane; lc < L.cn; lc += 32) lr_s[lr * TC + lc] = src[lc];
+    }
+    __syncthreads();
+    int nroots = 0;
+    for (int lr = wf; lr < L.rn; lr += NWF) {
+      for (int lc = lane; lc < L.cn; lc += 32) {
+        const int v = lr * TC + lc;
+        if (lr_s[v] == v) {  // a tile-local root
+          const int gv = (L.r0 + lr) * Ws + L.c0 + lc;
+          const int g = find_ro(parent, gv, limit);
+          nroots += (g == gv);
+          const int gi = g / Ws, gj = g - gi * Ws;
+          lab_s[v] = gi * W + gj * s;
+        }
+      }
+    }
+    const int cnt = __reduce_add_sync(FULL, nroots);
+    if (lane == 0 && cnt) atomicAdd(d->nseg, cnt);
+    __syncthreads();
+    if (s == 1) {
+      for (int lr = wf; lr < L.rn; lr += NWF) {
+        int32_t* dst = labels + (size_t)(L.r0 + lr) * W + L.c0;
+#pragma unroll 4
+        for (int lc = lane; lc < L.cn; lc += 32) {
+          const uint16_t r = lr_s[lr * TC + lc];
+          dst[lc] = r == NO_ROOT ? -1 : lab_s[r];
+        }
+      }
+    } else {
+      for (int lr = wf; lr < L.rn; lr += NWF) {
+        const int i = L.r0 + lr;
+        const int row = d->order[i];
+        for (int lc = lane; lc < L.cn; lc += 32) {
+          const int j = L.c0 + lc;
+          const uint16_t rl = lr_s[lr * TC + lc];
+          const int32_t lo = rl == NO_ROOT ? -1 : lab_s[rl];
+          labels[(size_t)i * W + (size_t)j * s] = lo;
+          // the s-1 points after column j*s
+          int jh = -1, cnext = 0;
+          if (j + 1 < Ws) {
+            jh = j + 1;
+            cnext = (j + 1) * s;
+          } else if (L.wrap) {
+            jh = 0;
+            cnext = W;
           }
-        } else {
-          bool ok;
-          if (d->valid) {
-            ok = d->valid[(size_t)i * W + c] != 0;
-          } else {
-            const int row = d->order[i];
-            float r = -1.f;
-            if ((unsigned)row < (unsigned)d->H) {
-              const size_t o = (size_t)row * W + c;
-              r = d->xyzr ? __ldg(&d->xyzr[o].w) : __ldg(d->range + o);
+          int32_t hi = -1;
+          if (jh >= 0) {
+            if (jh >= L.c0 && jh < L.c0 + L.cn) {
+              const uint16_t rh = lr_s[lr * TC + (jh - L.c0)];
+              hi = rh == NO_ROOT ? -1 : lab_s[rh];
+            } else {
+              hi = vertex_label_global<TR, TC>(lroot, parent, Ws, W, s, i, jh, limit);
             }
-            ok = in_range(r, d->r_min, d->r_max);
           }
-          if (!ok) {
-            lab = -1;
-          } else {
-            const int32_t lo = vertex_label(d, i, j, limit);
-            const int dlo = rem;
-            int32_t hi = -1;
-            int dhi = 0;
-            bool have_hi = false;
-            if (j + 1 < Ws) {
-              hi = vertex_label(d, i, j + 1, limit);
-              dhi = (j + 1) * s - c;
-              have_hi = true;
-            } else if (d->wrap) {
-              hi = vertex_label(d, i, 0, limit);
-              dhi = W - c;
-              have_hi = true;
+          const int cend = min((j + 1) * s, W);
+          for (int c = j * s + 1; c < cend; ++c) {
+            bool ok;
+            if (d->valid) {
+              ok = d->valid[(size_t)i * W + c] != 0;
+            } else {
+              float r = -1.f;
+              if ((unsigned)row < (unsigned)L.H) {
+                const size_t o = (size_t)row * W + c;
+                r = d->xyzr ? __ldg(&d->xyzr[o].w) : __ldg(d->range + o);
+              }
+              ok = in_range(r, d->r_min, d->r_max);
             }
-            int32_t first = lo, second = have_hi ? hi : -1;
-            if (have_hi && dhi < dlo) {
-              first = hi;
-              second = lo;
-            }
-            lab = first != -1 ? first : second;
+            labels[(size_t)i * W + c] = ok ? backfill(lo, c - j * s, hi, cnext - c, jh >= 0) : -1;
           }
         }
-        d->labels[(size_t)i * W + c] = lab;
       }
-      const int cnt = __reduce_add_sync(0xffffffffu, root);
-      if ((tid & 31) == 0 && cnt) atomicAdd(d->nseg, cnt);
     }
+    __syncthreads();
   }
 }
 
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-template <int TR, int TC>
+template <int TR, int NW>
 static cudaError_t set_attrs() {
-  return cudaFuncSetAttribute(k_tile<TR, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)Geo<TR, TC>::bytes);
+  cudaError_t e = cudaFuncSetAttribute(k_tile<TR, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)Geo<TR, NW>::bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_tile_ccl<TR, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)Geo<TR, NW>::ccl_bytes);
 }
 
 cudaError_t prepare_kernels() {
   cudaError_t e;
-  if ((e = set_attrs<8, 128>()) != cudaSuccess) return e;
-  if ((e = set_attrs<4, 256>()) != cudaSuccess) return e;
-  if ((e = set_attrs<16, 64>()) != cudaSuccess) return e;
-  if ((e = set_attrs<2, 512>()) != cudaSuccess) return e;
-  if ((e = set_attrs<8, 64>()) != cudaSuccess) return e;
+  if ((e = set_attrs<16, 4>()) != cudaSuccess) return e;
+  if ((e = set_attrs<32, 4>()) != cudaSuccess) return e;
+  if ((e = set_attrs<8, 8>()) != cudaSuccess) return e;
+  if ((e = set_attrs<16, 8>()) != cudaSuccess) return e;
+  if ((e = set_attrs<32, 8>()) != cudaSuccess) return e;
   return cudaSuccess;
 }
 
 cudaError_t launch_prep(const KArgs& a, cudaStream_t st) {
   const int n = a.scans ? a.nscans : 1;
-  k_prep<<<n, NT, 0, st>>>(a);
+  k_prep<<<n, NT_PREP, 0, st>>>(a);
   return cudaGetLastError();
 }
 
 #define LSG_DISPATCH(tile, FN, ...)                       \
   switch (tile) {                                         \
-    case LSG_TILE_4x256: return FN<4, 256>(__VA_ARGS__);  \
-    case LSG_TILE_16x64: return FN<16, 64>(__VA_ARGS__);  \
-    case LSG_TILE_2x512: return FN<2, 512>(__VA_ARGS__);  \
-    case LSG_TILE_8x64: return FN<8, 64>(__VA_ARGS__);    \
-    default: return FN<8, 128>(__VA_ARGS__);             \
+    case LSG_TILE_32x116: return FN<32, 4>(__VA_ARGS__);  \
+    case LSG_TILE_8x232: return FN<8, 8>(__VA_ARGS__);    \
+    case LSG_TILE_16x232: return FN<16, 8>(__VA_ARGS__);  \
+    case LSG_TILE_32x232: return FN<32, 8>(__VA_ARGS__);  \
+    default: return FN<16, 4>(__VA_ARGS__);               \
   }
 
-template <int TR, int TC>
+template <int TR, int NW>
 static cudaError_t run_tile(const KArgs& a, cudaStream_t st) {
-  k_tile<TR, TC><<<a.ntiles, NT, Geo<TR, TC>::bytes, st>>>(a);
+  k_tile<TR, NW><<<a.ntiles, NW * 32, Geo<TR, NW>::bytes, st>>>(a);
   return cudaGetLastError();
 }
-template <int TR, int TC>
+template <int TR, int NW>
 static cudaError_t run_tile_ccl(const KArgs& a, cudaStream_t st) {
-  k_tile_ccl<TR, TC><<<a.ntiles, NT, 0, st>>>(a);
+  k_tile_ccl<TR, NW><<<a.ntiles, NW * 32, Geo<TR, NW>::ccl_bytes, st>>>(a);
   return cudaGetLastError();
 }
-template <int TR, int TC>
+template <int TR, int NW>
 static cudaError_t run_merge(const KArgs& a, cudaStream_t st) {
-  k_merge<TR, TC><<<a.ntiles, NT, 0, st>>>(a);
+  k_merge<TR, NW><<<a.ntiles, NT_MERGE, 0, st>>>(a);
   return cudaGetLastError();
 }
-template <int TR, int TC>
+template <int TR, int NW>
 static cudaError_t run_flatten(const KArgs& a, cudaStream_t st) {
-  k_flatten<TR, TC><<<a.ntiles, NT, 0, st>>>(a);
+  k_flatten<TR, NW><<<a.ntiles, NT_FLAT, 0, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -8,8 +8,8 @@
 // side allocations by their plug-ins.  Such callers can still own their input
 // and output buffers but cannot let the library grow a workspace.
 //
-// How: the workspace (ring order, per-ring sin/cos, union-find parents and a
-// device error word) lives in one file-scope __device__ array of fixed size,
+// How: the workspace (ring order, per-ring sin/cos, union-find parents,
+// tile-local roots and a device error word) lives in one file-scope __device__ array of fixed size,
 // created when the library is loaded on a device and held until the process
 // exits.  Host code cannot use the array's name as a device address, so the
 // first call on each device looks the address up with cudaGetSymbolAddress
@@ -30,8 +30,10 @@ constexpr size_t kOrderOff = 0;                                         // int32
 constexpr size_t kTrigOff = kOrderOff + sizeof(int32_t) * LSG_MAX_RINGS;  // float2[LSG_MAX_RINGS]
 constexpr size_t kErrOff = kTrigOff + sizeof(float2) * LSG_MAX_RINGS;     // int32 error word
 constexpr size_t kParentOff = kErrOff + 256;                             // int32[max vertices]
-constexpr size_t kScratchBytes = kParentOff + sizeof(int32_t) * (size_t)LSG_NOALLOC_MAX_VERTICES;
-static_assert(kTrigOff % 256 == 0 && kErrOff % 256 == 0 && kParentOff % 256 == 0, "alignment");
+constexpr size_t kRootOff = kParentOff + sizeof(int32_t) * (size_t)LSG_NOALLOC_MAX_VERTICES;  // uint16[max]
+constexpr size_t kScratchBytes = kRootOff + sizeof(uint16_t) * (size_t)LSG_NOALLOC_MAX_VERTICES;
+static_assert(kTrigOff % 256 == 0 && kErrOff % 256 == 0 && kParentOff % 256 == 0 && kRootOff % 256 == 0,
+              "alignment");
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
@@ -75,10 +77,11 @@ extern "C" lsg_status lsg_segment_noalloc(const lsg_scan* scan, const lsg_params
   lsg::KArgs a;
   memset(&a, 0, sizeof(a));
   a.one = lsg::make_desc(scan, params, out, Ws);
-  lsg::set_tiles(a.one, LSG_TILE_8x128, 0);
+  lsg::set_tiles(a.one, LSG_TILE_16x116, 0);
   a.one.order = reinterpret_cast<int32_t*>(base + kOrderOff);
   a.one.trig = reinterpret_cast<float2*>(base + kTrigOff);
   a.one.parent = reinterpret_cast<int32_t*>(base + kParentOff);
+  a.one.lroot = reinterpret_cast<uint16_t*>(base + kRootOff);
   a.ntiles = a.one.tiles_r * a.one.tiles_c;
   a.nscans = 1;
   a.err = reinterpret_cast<int32_t*>(base + kErrOff);
@@ -86,8 +89,8 @@ extern "C" lsg_status lsg_segment_noalloc(const lsg_scan* scan, const lsg_params
   // everything else is fully written by the kernels before it is read.
   cudaError_t e = cudaMemsetAsync(a.err, 0, sizeof(int32_t), cs);
   if (e == cudaSuccess) e = lsg::launch_prep(a, cs);
-  if (e == cudaSuccess) e = lsg::launch_tile(LSG_TILE_8x128, a, cs);
-  if (e == cudaSuccess) e = lsg::launch_merge(LSG_TILE_8x128, a, cs);
-  if (e == cudaSuccess) e = lsg::launch_flatten(LSG_TILE_8x128, a, cs);
+  if (e == cudaSuccess) e = lsg::launch_tile(LSG_TILE_16x116, a, cs);
+  if (e == cudaSuccess) e = lsg::launch_merge(LSG_TILE_16x116, a, cs);
+  if (e == cudaSuccess) e = lsg::launch_flatten(LSG_TILE_16x116, a, cs);
   return e == cudaSuccess ? LSG_OK : LSG_E_CUDA;
 }

@@ -55,7 +55,7 @@ def run_gpu(ctx, scan, p, range_only=False, tile=None):
     torch.cuda.synchronize()
     assert ctx.error() == lsg.LSG_OK
     if tile is not None:
-        lsg.lsg_set_tile(ctx.h, lsg.TILES["8x128"])
+        lsg.lsg_set_tile(ctx.h, lsg.TILES["16x116"])
     return (out.meshbits.cpu().numpy(), out.normals.cpu().numpy(), out.labels.cpu().numpy(),
             int(out.nseg.cpu()[0]))
 
@@ -111,10 +111,10 @@ def test_component_predicate(ctx):
 
 RAGGED = [
     # (rings, cols, s, wrap, tile)
-    (1, 1, 1, 1, "8x128"), (1, 7, 1, 1, "8x128"), (2, 2, 1, 1, "8x128"), (3, 3, 1, 1, "8x64"),
-    (9, 131, 1, 1, "8x128"), (9, 131, 1, 0, "8x128"), (17, 257, 2, 1, "16x64"), (17, 257, 3, 0, "4x256"),
-    (5, 1030, 1, 1, "2x512"), (33, 129, 1, 1, "8x64"), (16, 1800, 5, 1, "8x128"), (7, 1000, 15, 1, "16x64"),
-    (64, 300, 1, 1, "4x256"), (3, 512, 2, 1, "2x512"), (24, 640, 4, 0, "8x64"),
+    (1, 1, 1, 1, "16x116"), (1, 7, 1, 1, "16x116"), (2, 2, 1, 1, "16x116"), (3, 3, 1, 1, "32x232"),
+    (9, 131, 1, 1, "16x116"), (9, 131, 1, 0, "16x116"), (17, 257, 2, 1, "8x232"), (17, 257, 3, 0, "32x116"),
+    (5, 1030, 1, 1, "16x232"), (33, 129, 1, 1, "32x232"), (16, 1800, 5, 1, "16x116"), (7, 1000, 15, 1, "8x232"),
+    (64, 300, 1, 1, "32x116"), (3, 512, 2, 1, "16x232"), (24, 640, 4, 0, "32x232"),
 ]
 
 
@@ -194,14 +194,14 @@ def test_label_from_mask_random_masks(ctx):
             flat[hom] |= hb
         mb = flat.reshape(H, Ws)
         want, nwant = O.label_from_mask(mb, valid_full, W, s, wrap)
-        for tile in ("8x128", "2x512", "16x64"):
+        for tile in ("16x116", "16x232", "8x232"):
             lsg.lsg_set_tile(ctx.h, lsg.TILES[tile])
             got, n = ctx.label_from_mask(torch.from_numpy(mb).to(dev), torch.from_numpy(valid_full).to(dev), W, s,
                                          wrap)
             torch.cuda.synchronize()
             assert np.array_equal(got.cpu().numpy(), want), (case, H, W, s, wrap, tile)
             assert int(n.cpu()[0]) == nwant
-    lsg.lsg_set_tile(ctx.h, lsg.TILES["8x128"])
+    lsg.lsg_set_tile(ctx.h, lsg.TILES["16x116"])
 
 
 def test_nan_elevation_is_flagged_not_faulted(ctx):
