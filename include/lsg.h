@@ -221,6 +221,43 @@ lsg_status lsg_label_from_mask(lsg_ctx* ctx, int32_t H, int32_t W, int32_t s, in
 lsg_status lsg_batch_plan(lsg_ctx* ctx, int32_t n, const lsg_scan* scans, const lsg_params* params,
                           const lsg_out* outs, int tile, lsg_plan** plan);
 
+/*
+ * Dynamic batch: one pass over n scans whose set changes from call to call
+ * (the serving path).  Same semantics and outputs as n lsg_segment calls, in
+ * four launches; the scans' descriptors go to the device through a pinned
+ * staging buffer of the context (two of them, alternated; a call waits until
+ * the copy out of the buffer it reuses has run).  The workspace of all n scans
+ * comes from the context, so one context serves one stream at a time.
+ */
+lsg_status lsg_batch_launch(lsg_ctx* ctx, int32_t n, const lsg_scan* scans, const lsg_params* params,
+                            const lsg_out* outs, lsg_stream stream);
+
+/* Host buffers of one scan for lsg_batch_launch_io (pinned memory lets the
+ * copies run asynchronously; any NULL output is skipped). */
+typedef struct {
+  const float* xyzr;      /* host [H][W][4] input */
+  const float* elevation; /* host [H] input */
+  int32_t* labels;        /* host [H][W] result, or NULL */
+  int32_t* nseg;          /* host [1] result, or NULL */
+  uint8_t* meshbits;      /* host [H][Ws] result, or NULL */
+  float* normals;         /* host [H][Ws][3] result, or NULL */
+} lsg_host_io;
+
+/*
+ * lsg_batch_launch with the host transfers of the serving path in the same
+ * call, all ordered on `stream`: every scan's x,y,z,r and elevations are
+ * copied from io[b] into the device buffers scans[b].xyzr and
+ * scans[b].elevation (which must be writable device memory), then the pass
+ * runs, then the results listed in io[b] are copied back.
+ */
+lsg_status lsg_batch_launch_io(lsg_ctx* ctx, int32_t n, const lsg_scan* scans, const lsg_params* params,
+                               const lsg_out* outs, const lsg_host_io* io, lsg_stream stream);
+
+/* Pre-sizes a context so that later calls with at most max_scans scans,
+ * max_tiles tiles and workspace_bytes of workspace allocate nothing (the
+ * workspace of a scan is 12*H + 6*H*Ws bytes, rounded up to 256 per array). */
+lsg_status lsg_reserve(lsg_ctx* ctx, size_t workspace_bytes, int32_t max_scans, int32_t max_tiles);
+
 /* Replays the plan's graph on `stream`. */
 lsg_status lsg_batch_run(lsg_plan* plan, lsg_stream stream);
 

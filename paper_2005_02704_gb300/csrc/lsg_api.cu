@@ -14,14 +14,25 @@
 
 using namespace lsg;
 
+// Pinned staging buffer for the descriptor tables of lsg_batch_launch; the
+// event marks when the device copy out of it has run.
+struct DynStage {
+  void* host = nullptr;
+  void* dev = nullptr;
+  size_t cap = 0;
+  cudaEvent_t copied = nullptr;
+};
+
 struct lsg_ctx {
   int device = 0;
   size_t budget = 0;        // 0 = unlimited
   size_t used = 0;          // bytes currently held (context workspace + plans)
-  void* ws = nullptr;       // single-scan workspace
+  void* ws = nullptr;       // single-scan / dynamic-batch workspace
   size_t ws_bytes = 0;
   int32_t* d_err = nullptr; // sticky device error word
   int tile = LSG_TILE_16x116;
+  DynStage stage[2];        // alternated by successive lsg_batch_launch calls
+  int next_stage = 0;
 };
 
 struct lsg_plan {
@@ -249,6 +260,11 @@ lsg_status lsg_destroy(lsg_ctx* ctx) {
   cudaDeviceSynchronize();
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->d_err) cudaFree(ctx->d_err);
+  for (DynStage& st : ctx->stage) {
+    if (st.host) cudaFreeHost(st.host);
+    if (st.dev) cudaFree(st.dev);
+    if (st.copied) cudaEventDestroy(st.copied);
+  }
   delete ctx;
   return LSG_OK;
 }
@@ -335,6 +351,141 @@ lsg_status lsg_get_error(lsg_ctx* ctx) {
   if (v & DERR_TIMEOUT) return LSG_E_TIMEOUT;
   if (v) return LSG_E_DEVICE;
   return LSG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// dynamic batch (a different set of scans on every call)
+// ---------------------------------------------------------------------------
+static lsg_status grow_stage(lsg_ctx* ctx, DynStage& sg, size_t need) {
+  if (sg.cap >= need) return LSG_OK;
+  const size_t cap = align_up(need * 2, 1 << 16);
+  if (ctx->budget && ctx->used - sg.cap + cap > ctx->budget) return LSG_E_BUDGET;
+  if (sg.copied) {
+    cudaError_t e = cudaEventSynchronize(sg.copied);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  if (sg.host) cudaFreeHost(sg.host);
+  if (sg.dev) cudaFree(sg.dev);
+  ctx->used -= sg.cap;
+  sg.host = sg.dev = nullptr;
+  sg.cap = 0;
+  cudaError_t e;
+  if ((e = cudaMallocHost(&sg.host, cap)) != cudaSuccess) return cuda_status(e);
+  if ((e = cudaMalloc(&sg.dev, cap)) != cudaSuccess) return cuda_status(e);
+  sg.cap = cap;
+  ctx->used += cap;
+  return LSG_OK;
+}
+
+lsg_status lsg_reserve(lsg_ctx* ctx, size_t workspace_bytes, int32_t max_scans, int32_t max_tiles) {
+  if (!ctx || max_scans < 0 || max_tiles < 0) return LSG_E_ARG;
+  DeviceGuard g(ctx->device);
+  lsg_status st = reserve(ctx, workspace_bytes > 0 ? workspace_bytes : 256);
+  const size_t need = align_up(sizeof(ScanDesc) * (size_t)max_scans, 256) + sizeof(int32_t) * (size_t)max_tiles;
+  for (int k = 0; k < 2 && st == LSG_OK; ++k) st = grow_stage(ctx, ctx->stage[k], need);
+  return st;
+}
+
+static lsg_status batch_launch(lsg_ctx* ctx, int32_t n, const lsg_scan* scans, const lsg_params* params,
+                               const lsg_out* outs, const lsg_host_io* io, lsg_stream stream);
+
+lsg_status lsg_batch_launch(lsg_ctx* ctx, int32_t n, const lsg_scan* scans, const lsg_params* params,
+                            const lsg_out* outs, lsg_stream stream) {
+  return batch_launch(ctx, n, scans, params, outs, nullptr, stream);
+}
+
+lsg_status lsg_batch_launch_io(lsg_ctx* ctx, int32_t n, const lsg_scan* scans, const lsg_params* params,
+                               const lsg_out* outs, const lsg_host_io* io, lsg_stream stream) {
+  if (!io) return LSG_E_ARG;
+  return batch_launch(ctx, n, scans, params, outs, io, stream);
+}
+
+static lsg_status batch_launch(lsg_ctx* ctx, int32_t n, const lsg_scan* scans, const lsg_params* params,
+                               const lsg_out* outs, const lsg_host_io* io, lsg_stream stream) {
+  if (!ctx || n < 1 || !scans || !params || !outs) return LSG_E_ARG;
+  std::vector<int> Ws(n);
+  size_t ws_total = 0;
+  int64_t ntiles = 0;
+  const TileShape ts = tile_shape(ctx->tile);
+  for (int b = 0; b < n; ++b) {
+    lsg_status st = check_scan(&scans[b], &params[b], &outs[b], &Ws[b]);
+    if (st != LSG_OK) return st;
+    ws_total += scan_ws_bytes(scans[b].rings, Ws[b]);
+    if (scans[b].rings > 0 && scans[b].cols > 0)
+      ntiles += (int64_t)((scans[b].rings + ts.rows - 1) / ts.rows) * ((Ws[b] + ts.cols - 1) / ts.cols);
+  }
+  if (ntiles > INT32_MAX) return LSG_E_SHAPE;
+  DeviceGuard g(ctx->device);
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+  lsg_status st = reserve(ctx, ws_total > 0 ? ws_total : 256);
+  if (st != LSG_OK) return st;
+  // descriptor table + tile table in one staging buffer
+  const size_t desc_bytes = align_up(sizeof(ScanDesc) * n, 256);
+  const size_t need = desc_bytes + sizeof(int32_t) * (size_t)(ntiles > 0 ? ntiles : 1);
+  DynStage& sg = ctx->stage[ctx->next_stage];
+  ctx->next_stage ^= 1;
+  cudaError_t e = cudaSuccess;
+  if (sg.copied) e = cudaEventSynchronize(sg.copied);  // the previous copy out of it is done
+  if (e != cudaSuccess) return cuda_status(e);
+  st = grow_stage(ctx, sg, need);
+  if (st != LSG_OK) return st;
+  if (!sg.copied && (e = cudaEventCreateWithFlags(&sg.copied, cudaEventDisableTiming)) != cudaSuccess)
+    return cuda_status(e);
+  if (io) {
+    // inputs host -> device, on the same stream ahead of the pass
+    for (int b = 0; b < n && e == cudaSuccess; ++b) {
+      const size_t pts = (size_t)scans[b].rings * scans[b].cols;
+      if (!pts) continue;
+      if (!io[b].xyzr || !io[b].elevation || !scans[b].xyzr) return LSG_E_ARG;
+      e = cudaMemcpyAsync(const_cast<float*>(scans[b].xyzr), io[b].xyzr, pts * 16, cudaMemcpyHostToDevice, cs);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(const_cast<float*>(scans[b].elevation), io[b].elevation, sizeof(float) * scans[b].rings,
+                            cudaMemcpyHostToDevice, cs);
+    }
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  ScanDesc* hd = static_cast<ScanDesc*>(sg.host);
+  int32_t* htile = reinterpret_cast<int32_t*>(static_cast<char*>(sg.host) + desc_bytes);
+  char* base = static_cast<char*>(ctx->ws);
+  int32_t t0 = 0;
+  for (int b = 0; b < n; ++b) {
+    ScanDesc d = make_desc(&scans[b], &params[b], &outs[b], Ws[b]);
+    carve_ws(d, base);
+    base += scan_ws_bytes(d.H, d.Ws);
+    set_tiles(d, ctx->tile, t0);
+    const int nt = (d.H && d.W) ? d.tiles_r * d.tiles_c : 0;
+    for (int k = 0; k < nt; ++k) htile[t0 + k] = b;
+    t0 += nt;
+    hd[b] = d;
+  }
+  e = cudaMemcpyAsync(sg.dev, sg.host, desc_bytes + sizeof(int32_t) * (size_t)t0, cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess) e = cudaEventRecord(sg.copied, cs);
+  if (e != cudaSuccess) return cuda_status(e);
+  KArgs a;
+  memset(&a, 0, sizeof(a));
+  a.scans = static_cast<const ScanDesc*>(sg.dev);
+  a.tile_scan = reinterpret_cast<const int32_t*>(static_cast<char*>(sg.dev) + desc_bytes);
+  a.ntiles = t0;
+  a.nscans = n;
+  a.err = ctx->d_err;
+  e = launch_prep(a, cs);
+  if (e == cudaSuccess && t0 > 0) e = launch_tile(ctx->tile, a, cs);
+  if (e == cudaSuccess && t0 > 0) e = launch_merge(ctx->tile, a, cs);
+  if (e == cudaSuccess && t0 > 0) e = launch_flatten(ctx->tile, a, cs);
+  if (io) {
+    // results device -> host, behind the pass
+    for (int b = 0; b < n && e == cudaSuccess; ++b) {
+      const size_t pts = (size_t)scans[b].rings * scans[b].cols, nv = (size_t)scans[b].rings * Ws[b];
+      if (io[b].nseg) e = cudaMemcpyAsync(io[b].nseg, outs[b].nseg, sizeof(int32_t), cudaMemcpyDeviceToHost, cs);
+      if (e == cudaSuccess && io[b].labels && pts)
+        e = cudaMemcpyAsync(io[b].labels, outs[b].labels, pts * 4, cudaMemcpyDeviceToHost, cs);
+      if (e == cudaSuccess && io[b].meshbits && nv)
+        e = cudaMemcpyAsync(io[b].meshbits, outs[b].meshbits, nv, cudaMemcpyDeviceToHost, cs);
+      if (e == cudaSuccess && io[b].normals && nv)
+        e = cudaMemcpyAsync(io[b].normals, outs[b].normals, nv * 12, cudaMemcpyDeviceToHost, cs);
+    }
+  }
+  return cuda_status(e);
 }
 
 // ---------------------------------------------------------------------------

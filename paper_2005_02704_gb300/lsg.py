@@ -46,6 +46,11 @@ class lsg_out(ctypes.Structure):
                 ("labels", ctypes.c_void_p), ("nseg", ctypes.c_void_p)]
 
 
+class lsg_host_io(ctypes.Structure):
+    _fields_ = [("xyzr", ctypes.c_void_p), ("elevation", ctypes.c_void_p), ("labels", ctypes.c_void_p),
+                ("nseg", ctypes.c_void_p), ("meshbits", ctypes.c_void_p), ("normals", ctypes.c_void_p)]
+
+
 class LsgError(RuntimeError):
     def __init__(self, status: int, what: str):
         super().__init__(f"{what}: {lsg_status_str(status)} ({status})")
@@ -73,6 +78,11 @@ def load(build: bool = True):
             "lsg_batch_plan": (ctypes.c_int, [_P, I32, ctypes.POINTER(lsg_scan), ctypes.POINTER(lsg_params),
                                               ctypes.POINTER(lsg_out), ctypes.c_int, ctypes.POINTER(_P)]),
             "lsg_batch_run": (ctypes.c_int, [_P, _P]),
+            "lsg_batch_launch": (ctypes.c_int, [_P, I32, ctypes.POINTER(lsg_scan), ctypes.POINTER(lsg_params),
+                                                ctypes.POINTER(lsg_out), _P]),
+            "lsg_batch_launch_io": (ctypes.c_int, [_P, I32, ctypes.POINTER(lsg_scan), ctypes.POINTER(lsg_params),
+                                                   ctypes.POINTER(lsg_out), ctypes.POINTER(lsg_host_io), _P]),
+            "lsg_reserve": (ctypes.c_int, [_P, ctypes.c_size_t, I32, I32]),
             "lsg_autotune": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_int),
                                             ctypes.POINTER(ctypes.c_float)]),
             "lsg_plan_tile": (ctypes.c_int, [_P]),
@@ -146,6 +156,32 @@ def lsg_batch_plan(ctx: int, scans: Sequence[lsg_scan], params: Sequence[lsg_par
 
 def lsg_batch_run(plan: int, stream: int = 0) -> int:
     return load().lsg_batch_run(plan, stream or None)
+
+
+def lsg_batch_launch(ctx: int, scans, params, outs, stream: int = 0) -> int:
+    """One pass over a changing set of scans (arrays of lsg_scan / lsg_params /
+    lsg_out, or ctypes arrays of them).  Returns the status code."""
+    n = len(scans)
+    sa = scans if isinstance(scans, ctypes.Array) else (lsg_scan * n)(*scans)
+    pa = params if isinstance(params, ctypes.Array) else (lsg_params * n)(*params)
+    oa = outs if isinstance(outs, ctypes.Array) else (lsg_out * n)(*outs)
+    return load().lsg_batch_launch(ctx, n, sa, pa, oa, stream or None)
+
+
+def lsg_batch_launch_io(ctx: int, scans, params, outs, io, stream: int = 0) -> int:
+    """lsg_batch_launch plus the host->device input and device->host result
+    copies of each scan (ctypes arrays).  Returns the status code."""
+    return load().lsg_batch_launch_io(ctx, len(scans), scans, params, outs, io, stream or None)
+
+
+def lsg_reserve(ctx: int, workspace_bytes: int, max_scans: int, max_tiles: int) -> None:
+    _check(load().lsg_reserve(ctx, workspace_bytes, max_scans, max_tiles), "lsg_reserve")
+
+
+def scan_workspace_bytes(H: int, Ws: int) -> int:
+    """Workspace of one scan inside a batch (four arrays, 256-byte aligned)."""
+    up = lambda x: (x + 255) // 256 * 256
+    return up(4 * H) + up(8 * H) + up(4 * H * Ws) + up(2 * H * Ws)
 
 
 def lsg_autotune(plan: int, reps: int = 3, stream: int = 0):

@@ -1,0 +1,388 @@
+"""Serving path: continuous batching of scans from many sensors.
+
+Scans arrive one by one (several sensors, each at its own rate).  The server
+admits a scan as soon as a device slot for its shape is free or can be
+allocated within the memory budget (admission by device memory), keeps slots
+resident and reuses them for later scans of the same shape, and runs admitted
+scans in batches on several CUDA streams ("lanes"): whenever a lane is idle
+it takes every admitted scan waiting (up to ``max_batch``) and launches one
+batched pass (``lsg_batch_launch``) for them, so scans that arrive while
+others are on the GPU join the next batch and their work overlaps on the
+device.  Each batch uploads its inputs, segments them, and copies labels and
+segment counts back to pinned host memory on its lane's stream; a request is
+complete when the host sees that stream's event.
+
+The scheduler runs on the host; every step of the segmentation runs in the
+library's kernels.  ``SlotPool`` holds the admission logic and is testable
+without a GPU.
+"""
+from __future__ import annotations
+
+import collections
+import ctypes
+import math
+import time
+from dataclasses import dataclass, field
+from typing import Callable, Dict, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+from . import lsg
+
+ShapeKey = Tuple[int, int, int]  # rings, cols, subsample
+
+
+def slot_bytes(key: ShapeKey) -> int:
+    """Device bytes of one slot: inputs, outputs and the request's share of
+    the batch workspace (ring order, sin/cos, union-find parents, tile roots)."""
+    H, W, s = key
+    Ws = lsg.ws_of(W, s)
+    inputs = H * W * 16 + H * 4
+    outputs = H * Ws * (1 + 12) + H * W * 4 + 4
+    workspace = H * 12 + H * Ws * 6
+    return inputs + outputs + workspace
+
+
+class SlotPool:
+    """Resident device slots per scan shape under a byte budget.
+
+    acquire(key) returns a free slot of that shape, allocating one when the
+    budget allows (freeing idle slots of other shapes first if needed), or
+    None when the request must wait.  release(slot) makes it free again.
+    """
+
+    def __init__(self, budget_bytes: int, alloc: Callable[[ShapeKey], object],
+                 size_of: Callable[[ShapeKey], int] = slot_bytes, free_fn: Callable[[object], None] = None):
+        self.budget = int(budget_bytes)
+        self.alloc = alloc
+        self.size_of = size_of
+        self.free_fn = free_fn or (lambda s: None)
+        self.free: Dict[ShapeKey, List[object]] = collections.defaultdict(list)
+        self.used = 0
+        self.live = 0        # slots handed out
+        self.allocated = 0   # slots in existence
+        self.peak = 0
+
+    def acquire(self, key: ShapeKey):
+        lst = self.free.get(key)
+        if lst:
+            self.live += 1
+            return lst.pop()
+        need = self.size_of(key)
+        if need > self.budget:
+            raise ValueError(f"a scan of shape {key} needs {need} bytes, more than the budget {self.budget}")
+        if self.used + need > self.budget:
+            # evict idle slots of other shapes, largest first
+            idle = sorted(((self.size_of(k), k) for k, v in self.free.items() for _ in v), reverse=True)
+            for sz, k in idle:
+                if self.used + need <= self.budget:
+                    break
+                if k == key or not self.free[k]:
+                    continue
+                self.free_fn(self.free[k].pop())
+                self.used -= sz
+                self.allocated -= 1
+        if self.used + need > self.budget:
+            return None
+        slot = self.alloc(key)
+        self.used += need
+        self.allocated += 1
+        self.live += 1
+        self.peak = max(self.peak, self.used)
+        return slot
+
+    def release(self, key: ShapeKey, slot) -> None:
+        self.live -= 1
+        self.free[key].append(slot)
+
+
+@dataclass
+class Request:
+    ticket: int
+    sensor: int
+    key: ShapeKey
+    host_xyzr: "torch.Tensor"      # pinned float32 [H, W, 4]
+    host_elev: "torch.Tensor"      # pinned float32 [H]
+    az0: float
+    daz: float
+    params: "lsg.Params"
+    t_arrival: float               # wall clock (perf_counter)
+    t_launch: float = 0.0
+    t_done: float = 0.0
+    slot: object = None
+    keep_geometry: bool = False
+    result: Optional[dict] = None
+    c_params: object = None        # cached lsg_params of the sensor
+
+
+class Slot:
+    """Device buffers of one request (inputs, outputs), pinned host buffers
+    for its results, and the C descriptors pointing at them."""
+
+    def __init__(self, key: ShapeKey, device):
+        import torch
+        H, W, s = key
+        self.key = key
+        self.xyzr = torch.empty((H, W, 4), dtype=torch.float32, device=device)
+        self.elev = torch.empty(H, dtype=torch.float32, device=device)
+        self.out = lsg.alloc_outputs(H, W, s, device)
+        self.h_labels = torch.empty((H, W), dtype=torch.int32, pin_memory=True)
+        self.h_nseg = torch.empty(1, dtype=torch.int32, pin_memory=True)
+        self.h_meshbits = None
+        self.h_normals = None
+        self.c_out = self.out.to_c()
+        self.c_scan = lsg.make_scan(self.elev, self.xyzr, None, 0.0, 0.0)
+        self.c_io = lsg.lsg_host_io()
+        self.c_io.labels = self.h_labels.data_ptr() if self.h_labels.numel() else None
+        self.c_io.nseg = self.h_nseg.data_ptr()
+
+    def geometry_buffers(self):
+        import torch
+        if self.h_meshbits is None:
+            self.h_meshbits = torch.empty(tuple(self.out.meshbits.shape), dtype=torch.uint8, pin_memory=True)
+            self.h_normals = torch.empty(tuple(self.out.normals.shape), dtype=torch.float32, pin_memory=True)
+        return self.h_meshbits, self.h_normals
+
+
+class Server:
+    """Continuous-batching server on one GPU."""
+
+    def __init__(self, budget_bytes: int = 8 << 30, lanes: int = 3, max_batch: int = 64, device: int = 0,
+                 max_shape: ShapeKey = (128, 4096, 1)):
+        import torch
+        self.torch = torch
+        self.device = torch.device("cuda", device)
+        self.max_batch = max_batch
+        self.ctxs = [lsg.Context(device) for _ in range(lanes)]
+        # size every lane's workspace and staging for a full batch of the
+        # largest expected scan, so that serving allocates nothing
+        H, W, s_ = max_shape
+        Ws = lsg.ws_of(W, s_)
+        tiles = ((H + 7) // 8 + 1) * (Ws // 116 + 1)
+        for c in self.ctxs:
+            lsg.lsg_reserve(c.h, max_batch * lsg.scan_workspace_bytes(H, Ws), max_batch, 2 * max_batch * tiles)
+        self.streams = [torch.cuda.Stream(device=self.device) for _ in range(lanes)]
+        self.events = [torch.cuda.Event() for _ in range(lanes)]
+        self.inflight: List[Optional[List[Request]]] = [None] * lanes
+        self.pool = SlotPool(budget_bytes, lambda k: Slot(k, self.device))
+        self.pending: collections.deque = collections.deque()
+        self.done: List[Request] = []
+        self.batches = 0
+        self.batch_sizes: List[int] = []
+
+    def submit(self, req: Request) -> None:
+        self.pending.append(req)
+
+    def busy(self) -> bool:
+        return bool(self.pending) or any(b is not None for b in self.inflight)
+
+    def _reap(self) -> None:
+        for k, batch in enumerate(self.inflight):
+            if batch is None or not self.events[k].query():
+                continue
+            now = time.perf_counter()
+            for req in batch:
+                req.t_done = now
+                slot = req.slot
+                if req.keep_geometry:
+                    req.result = {"labels": slot.h_labels.clone(), "nseg": int(slot.h_nseg[0]),
+                                  "meshbits": slot.h_meshbits.clone(), "normals": slot.h_normals.clone()}
+                else:
+                    req.result = {"nseg": int(slot.h_nseg[0])}
+                self.pool.release(req.key, slot)
+                req.slot = None
+                self.done.append(req)
+            self.inflight[k] = None
+
+    def _launch(self, k: int) -> bool:
+        batch: List[Request] = []
+        while self.pending and len(batch) < self.max_batch:
+            req = self.pending[0]
+            slot = self.pool.acquire(req.key)
+            if slot is None:
+                break  # admission waits for memory (first come, first served)
+            self.pending.popleft()
+            req.slot = slot
+            batch.append(req)
+        if not batch:
+            return False
+        st = self.streams[k]
+        now = time.perf_counter()
+        n = len(batch)
+        scans = (lsg.lsg_scan * n)()
+        params = (lsg.lsg_params * n)()
+        outs = (lsg.lsg_out * n)()
+        io = (lsg.lsg_host_io * n)()
+        for b, req in enumerate(batch):
+            slot = req.slot
+            req.t_launch = now
+            sc = slot.c_scan
+            sc.azimuth0 = req.az0
+            sc.azimuth_step = req.daz
+            scans[b] = sc
+            params[b] = req.c_params if req.c_params is not None else req.params.to_c()
+            outs[b] = slot.c_out
+            h = slot.c_io
+            h.xyzr = req.host_xyzr.data_ptr()
+            h.elevation = req.host_elev.data_ptr()
+            if req.keep_geometry:
+                mbh, nrh = slot.geometry_buffers()
+                h.meshbits = mbh.data_ptr() if mbh.numel() else None
+                h.normals = nrh.data_ptr() if nrh.numel() else None
+            else:
+                h.meshbits = None
+                h.normals = None
+            io[b] = h
+        # uploads, the batched pass and the result downloads, on this lane
+        rc = lsg.lsg_batch_launch_io(self.ctxs[k].h, scans, params, outs, io, int(st.cuda_stream))
+        if rc != lsg.LSG_OK:
+            raise lsg.LsgError(rc, "lsg_batch_launch_io")
+        self.events[k].record(st)
+        self.inflight[k] = batch
+        self.batches += 1
+        self.batch_sizes.append(n)
+        return True
+
+    def poll(self) -> None:
+        """Reap finished batches, then launch waiting scans on idle lanes."""
+        self._reap()
+        for k in range(len(self.inflight)):
+            if self.inflight[k] is None and self.pending:
+                self._launch(k)
+
+    def drain(self) -> None:
+        while self.busy():
+            self.poll()
+
+    def close(self) -> None:
+        self.torch.cuda.synchronize()
+        for c in self.ctxs:
+            c.close()
+
+
+# --------------------------------------------------------------------------
+# sensor simulation and the two serving loops
+# --------------------------------------------------------------------------
+@dataclass
+class SensorFeed:
+    """One simulated sensor: its scans (pinned host copies) and rate."""
+    sensor: int
+    key: ShapeKey
+    rate_hz: float
+    host_xyzr: List["torch.Tensor"]
+    host_elev: "torch.Tensor"
+    az0: float
+    daz: float
+    params: "lsg.Params"
+    c_params: object = None
+
+
+def arrival_trace(rates: Sequence[float], duration_s: float = 60.0, burst=(30.0, 40.0, 4.0),
+                  seed: int = 7) -> List[Tuple[float, int]]:
+    """Poisson arrivals (exponential gaps) per sensor, with the rate multiplied
+    by burst[2] inside [burst[0], burst[1]).  Returns sorted (time, sensor)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k, r in enumerate(rates):
+        t = float(rng.uniform(0.0, 1.0 / r))
+        while t < duration_s:
+            out.append((t, k))
+            rate = r * (burst[2] if burst and burst[0] <= t < burst[1] else 1.0)
+            t += float(rng.exponential(1.0 / rate))
+    out.sort()
+    return out
+
+
+def _request(feed: SensorFeed, ticket: int, t_arrival: float, keep_geometry: bool = False) -> Request:
+    x = feed.host_xyzr[ticket % len(feed.host_xyzr)]
+    if feed.c_params is None:
+        feed.c_params = feed.params.to_c()
+    return Request(ticket, feed.sensor, feed.key, x, feed.host_elev, feed.az0, feed.daz, feed.params, t_arrival,
+                   keep_geometry=keep_geometry, c_params=feed.c_params)
+
+
+def run_served(server: Server, feeds: Sequence[SensorFeed], trace, time_scale: float,
+               keep_geometry: bool = False) -> dict:
+    """Replays the trace (virtual seconds / time_scale = wall seconds) through
+    the server; returns latency and throughput statistics."""
+    t0 = time.perf_counter()
+    i = 0
+    reqs = []
+    while i < len(trace) or server.busy():
+        now = time.perf_counter()
+        while i < len(trace) and trace[i][0] / time_scale <= now - t0:
+            tv, k = trace[i]
+            r = _request(feeds[k], i, t0 + tv / time_scale, keep_geometry)
+            reqs.append(r)
+            server.submit(r)
+            i += 1
+        server.poll()
+    t1 = time.perf_counter()
+    return summarize(reqs, t1 - t0)
+
+
+def run_serial(feeds: Sequence[SensorFeed], trace, time_scale: float, device: int = 0) -> dict:
+    """The plain per-scan loop: one scan at a time in arrival order (upload,
+    lsg_segment, download, synchronise), on one stream."""
+    import torch
+    dev = torch.device("cuda", device)
+    ctx = lsg.Context(device)
+    slots: Dict[ShapeKey, Slot] = {}
+    stream = torch.cuda.current_stream(dev)
+    t0 = time.perf_counter()
+    reqs = []
+    for i, (tv, k) in enumerate(trace):
+        arrival = t0 + tv / time_scale
+        while time.perf_counter() < arrival:
+            pass
+        feed = feeds[k]
+        r = _request(feed, i, arrival)
+        slot = slots.get(feed.key)
+        if slot is None:
+            slot = slots[feed.key] = Slot(feed.key, dev)
+        r.t_launch = time.perf_counter()
+        slot.xyzr.copy_(r.host_xyzr, non_blocking=True)
+        slot.elev.copy_(r.host_elev, non_blocking=True)
+        ctx.segment(slot.elev, xyzr=slot.xyzr, az0=r.az0, daz=r.daz, params=r.params, out=slot.out,
+                    stream=stream)
+        slot.h_labels.copy_(slot.out.labels, non_blocking=True)
+        slot.h_nseg.copy_(slot.out.nseg, non_blocking=True)
+        stream.synchronize()
+        r.t_done = time.perf_counter()
+        reqs.append(r)
+    t1 = time.perf_counter()
+    ctx.close()
+    return summarize(reqs, t1 - t0)
+
+
+def summarize(reqs: Sequence[Request], wall_s: float) -> dict:
+    lat = np.array([(r.t_done - r.t_arrival) * 1e3 for r in reqs]) if reqs else np.zeros(1)
+    pts = sum(r.key[0] * r.key[1] for r in reqs)
+    return {"scans": len(reqs), "points": pts, "wall_s": wall_s, "scans_per_s": len(reqs) / wall_s,
+            "points_per_s": pts / wall_s, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat.max())}
+
+
+def make_feeds(specs, scans_per_sensor: int = 4, seed: int = 11) -> List[SensorFeed]:
+    """Sensors from lidarsim specs: each gets `scans_per_sensor` ray-cast scans
+    (pinned host memory) and a rate drawn from 10-20 Hz."""
+    import torch
+    import lidarsim
+    from dataclasses import replace
+    rng = np.random.default_rng(seed)
+    feeds = []
+    for k, sp in enumerate(specs):
+        xs = []
+        scan = None
+        for m in range(scans_per_sensor):
+            scan = lidarsim.make_scan(replace(sp, seed=sp.seed * 1000 + m))
+            t = torch.empty(scan.xyzr.shape, dtype=torch.float32, pin_memory=True)
+            t.numpy()[:] = scan.xyzr
+            xs.append(t)
+        e = torch.empty(scan.elev.shape, dtype=torch.float32, pin_memory=True)
+        e.numpy()[:] = scan.elev
+        p = lsg.Params(subsample=sp.subsample, r_max=sp.r_max, jump_rel_h=sp.jump_rel_h, jump_rel_v=sp.jump_rel_v,
+                       angle_rad=math.radians(sp.angle_deg))
+        feeds.append(SensorFeed(k, (scan.rings, scan.cols, sp.subsample), float(rng.uniform(10.0, 20.0)), xs, e,
+                                scan.az0, scan.daz, p))
+    return feeds
