@@ -68,10 +68,8 @@ def parse():
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    from paper_2005_02704_gb300 import replicas
+    return replicas.env()
 
 
 # --------------------------------------------------------------------------
@@ -164,7 +162,8 @@ def profiled_traffic():
 
 def batch_data(n, rank):
     import lidarsim
-    specs = lidarsim.batch_specs(n, seed0=2000 + rank * n)
+    from paper_2005_02704_gb300 import replicas
+    specs = lidarsim.batch_specs(n, seed0=replicas.shard_seed0(rank, n))
     scans = [lidarsim.make_scan(sp) for sp in specs]
     return specs, scans
 
@@ -290,28 +289,13 @@ def main():
     import torch
     import torch.distributed as dist
 
+    from paper_2005_02704_gb300 import replicas
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
-    def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    def sum_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+    red = replicas.Reducer(world, device=torch.device("cuda", local))
+    barrier, max_over_ranks, sum_over_ranks = red.barrier, red.max, red.sum
 
     from paper_2005_02704_gb300 import batch, lsg
     lsg.load()
