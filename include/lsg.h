@@ -158,9 +158,9 @@ enum {
   LSG_TILE_AUTO = -1,
   LSG_TILE_16x116 = 0,
   LSG_TILE_32x116 = 1,
-  LSG_TILE_8x232 = 2,
-  LSG_TILE_16x232 = 3,
-  LSG_TILE_32x232 = 4,
+  LSG_TILE_32x232 = 2,
+  LSG_TILE_64x116 = 3,
+  LSG_TILE_64x232 = 4,
   LSG_TILE_COUNT = 5
 };
 

@@ -151,9 +151,11 @@ void set_tiles(ScanDesc& d, int tile, int tile0) {
 
 namespace {
 
+// tile-root rows are padded to a multiple of 8 entries (see root_pitch)
 size_t scan_ws_bytes(int H, int Ws) {
+  const size_t lp = (size_t)((Ws + 7) & ~7);
   return align_up(sizeof(int32_t) * H, 256) + align_up(sizeof(float2) * H, 256) +
-         align_up(sizeof(int32_t) * (size_t)H * Ws, 256) + align_up(sizeof(uint16_t) * (size_t)H * Ws, 256);
+         align_up(sizeof(int32_t) * (size_t)H * Ws, 256) + align_up(sizeof(uint16_t) * (size_t)H * lp, 256);
 }
 
 void carve_ws(ScanDesc& d, char* base) {
@@ -571,10 +573,10 @@ lsg_status lsg_batch_plan(lsg_ctx* ctx, int32_t n, const lsg_scan* scans, const 
     if (st != LSG_OK) return st;
     ws_total += scan_ws_bytes(scans[b].rings, Ws[b]);
   }
-  // bound on the tile table over every tile shape (at least 8 rows x 116 columns)
+  // bound on the tile table over every tile shape (at least 16 rows x 116 columns)
   size_t tiles_max = 0;
   for (int b = 0; b < n; ++b)
-    tiles_max += (size_t)(scans[b].rings / 8 + 1) * (Ws[b] / 116 + 1);
+    tiles_max += (size_t)(scans[b].rings / 16 + 1) * (Ws[b] / 116 + 1);
   const size_t bytes = ws_total + align_up(sizeof(ScanDesc) * n, 256) + sizeof(int32_t) * tiles_max;
   if (ctx->budget && ctx->used + bytes > ctx->budget) return LSG_E_BUDGET;
   DeviceGuard g(ctx->device);

@@ -31,6 +31,7 @@
 // each component's root is its smallest vertex index whatever the thread
 // order, and a tile-local root is the smallest index of its tile component.
 #include <cuda_runtime.h>
+#include <limits.h>
 #include <stdint.h>
 
 #include "lsg_internal.h"
@@ -44,12 +45,16 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr int SO = 29;  // output columns per warp strip (lanes 1..29)
 constexpr uint16_t NO_ROOT = 0xFFFF;  // tile-local root of a vertex out of range
 
+// Row pitch of the tile-root array: Ws rounded up to 8 entries (16 bytes), so
+// that a tile's rows can be read with aligned vector loads.
+__host__ __device__ __forceinline__ int root_pitch(int Ws) { return (Ws + 7) & ~7; }
+
 TileShape tile_shape(int tile) {
   switch (tile) {
     case LSG_TILE_32x116: return {32, 116};
-    case LSG_TILE_8x232: return {8, 232};
-    case LSG_TILE_16x232: return {16, 232};
     case LSG_TILE_32x232: return {32, 232};
+    case LSG_TILE_64x116: return {64, 116};
+    case LSG_TILE_64x232: return {64, 232};
     case LSG_TILE_16x116:
     default: return {16, 116};
   }
@@ -77,17 +82,14 @@ __device__ __forceinline__ float vlen(float x, float y, float z) {
 
 // One weighted triangle term of the normal sum (Sec. 2, normal estimation):
 // w (a x b) with w = 1 / (|a| + |b|), added only when the triangle exists.
-// Spokes of missing triangles may point at absent points, so their term is
-// dropped after the arithmetic instead of being multiplied by zero.
+// The sweep zeroes the coordinates of points out of range, so every spoke is
+// finite and a missing triangle's term is removed by a zero weight.
 __device__ __forceinline__ void tri_term(float ax, float ay, float az, float la, float bx, float by, float bz,
                                          float lb, bool exists, float& sx, float& sy, float& sz) {
-  const float w = __frcp_rn(la + lb);
-  const float tx = w * (ay * bz - az * by);
-  const float ty = w * (az * bx - ax * bz);
-  const float tz = w * (ax * by - ay * bx);
-  sx += exists ? tx : 0.f;
-  sy += exists ? ty : 0.f;
-  sz += exists ? tz : 0.f;
+  const float w = exists ? __fdividef(1.0f, la + lb) : 0.f;  // hardware reciprocal, <= 2 ulp
+  sx = fmaf(w, ay * bz - az * by, sx);
+  sy = fmaf(w, az * bx - ax * bz, sy);
+  sz = fmaf(w, ax * by - ay * bx, sz);
 }
 
 // Homogeneity predicate of Algorithm 1 between two vertices' normals
@@ -215,20 +217,45 @@ __global__ void __launch_bounds__(NT_PREP) k_prep(const __grid_constant__ KArgs 
 // ---------------------------------------------------------------------------
 // tile geometry
 // ---------------------------------------------------------------------------
+constexpr int RING = 8;  // rows each lane keeps in flight (cp.async depth)
+
 template <int TR, int NW>
 struct Geo {
   static constexpr int NT = NW * 32;
   static constexpr int TC = NW * SO;             // output columns of a tile
-  static constexpr int HR = TR + 3;              // staged rows  r0-1 .. r0+TR+1
-  static constexpr int HC = TC + 3;              // staged cols  c0-1 .. c0+TC+1
+  static constexpr int HR = TR + 3;              // rows read: r0-1 .. r0+TR+1
   static constexpr int NV = TR * TC;
-  static constexpr size_t off_hx = 0;
-  static constexpr size_t off_lp = off_hx + sizeof(float4) * HR * HC;
-  static constexpr size_t off_tb = off_lp + sizeof(int) * NV;
-  static constexpr size_t off_tg = off_tb + ((NV + 15) / 16) * 16;
-  static constexpr size_t bytes = off_tg + sizeof(float2) * HC;
+  static constexpr size_t off_ring = 0;          // per-warp row rings [NW][RING+1][32] float4
+  static constexpr size_t off_lp = off_ring + sizeof(float4) * NW * (RING + 1) * 32;  // tile union-find
+  static constexpr size_t off_tb = off_lp + sizeof(int) * NV;  // tile mesh bytes
+  static constexpr size_t bytes = off_tb + ((NV + 15) / 16) * 16;
   static constexpr size_t ccl_bytes = sizeof(int) * NV + ((NV + 15) / 16) * 16;
 };
+
+// Issue the asynchronous copy of scan row i at the lane's column into its
+// ring slot (x,y,z,r input), or store the decoded / absent value directly.
+__device__ __forceinline__ void fetch_point(float4* slot, const float4* __restrict__ xyzr,
+                                            const float* __restrict__ range, const int32_t* __restrict__ order,
+                                            const float2* __restrict__ trig, int H, int W, int i, bool colok,
+                                            size_t coff, float sp, float cp) {
+  if (colok && i >= 0 && i < H) {
+    const int row = __ldg(order + i);
+    if ((unsigned)row < (unsigned)H) {
+      const size_t o = (size_t)row * W + coff;
+      if (xyzr) {
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(slot);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(xyzr + o) : "memory");
+      } else {
+        const float r = __ldg(range + o);
+        const float2 te = __ldg(trig + i);
+        const float rc = r * te.y;
+        *slot = make_float4(rc * cp, rc * sp, r * te.x, r);
+      }
+      return;
+    }
+  }
+  *slot = make_float4(0.f, 0.f, 0.f, -1.f);
+}
 
 // Everything of a descriptor the tile kernels use, in registers.
 struct Loc {
@@ -251,6 +278,11 @@ __device__ __forceinline__ Loc make_loc(const ScanDesc* d, int lt, int TR, int T
   L.cn = min(TC, L.Ws - L.c0);
   return L;
 }
+
+template <int TR, int NW>
+__device__ __forceinline__ void tile_cross_and_roots(const Loc& L, const uint8_t* __restrict__ tb, int* lp,
+                                                     uint16_t* __restrict__ lroot, int32_t* __restrict__ parent,
+                                                     int32_t* err);
 
 // Tile components of the tile bytes tb[TR][TC] (mesh + homogeneity bits of
 // the tile's own vertices): horizontal runs from a ballot, vertical joins in a
@@ -297,8 +329,19 @@ __device__ __forceinline__ void tile_components(const Loc& L, const uint8_t* __r
     bprev = b;
   }
   __syncthreads();
+  tile_cross_and_roots<TR, NW>(L, tb, lp, lroot, parent, err);
+}
 
-  // C2: edges across strip borders, and the seam of a tile spanning the ring
+// C2: edges across strip borders, and the seam of a tile spanning the ring;
+// C3: every vertex's tile-local root (vertices out of range: NO_ROOT), roots
+// marked in the global union-find.
+template <int TR, int NW>
+__device__ __forceinline__ void tile_cross_and_roots(const Loc& L, const uint8_t* __restrict__ tb, int* lp,
+                                                     uint16_t* __restrict__ lroot, int32_t* __restrict__ parent,
+                                                     int32_t* err) {
+  using G = Geo<TR, NW>;
+  constexpr int TC = G::TC;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const bool full_ring = L.wrap && L.c0 == 0 && L.cn == L.Ws;
   for (int idx = threadIdx.x; idx < L.rn * NW; idx += G::NT) {
     const int lr = idx / NW, b = idx - (idx / NW) * NW;
@@ -324,12 +367,13 @@ __device__ __forceinline__ void tile_components(const Loc& L, const uint8_t* __r
     for (int lc = lane; lc < L.cn; lc += 32) {
       const int v = lr * TC + lc;
       const size_t gv = (size_t)(L.r0 + lr) * L.Ws + (L.c0 + lc);
+      const size_t gr = (size_t)(L.r0 + lr) * root_pitch(L.Ws) + (L.c0 + lc);
       if (!(tb[v] & B_VALID)) {
-        lroot[gv] = NO_ROOT;
+        lroot[gr] = NO_ROOT;
         continue;
       }
       const int r = find_s(lp, v, G::NV + 1);
-      lroot[gv] = (uint16_t)r;
+      lroot[gr] = (uint16_t)r;
       if (r == v) parent[gv] = (int32_t)gv;
     }
   }
@@ -341,13 +385,12 @@ __device__ __forceinline__ void tile_components(const Loc& L, const uint8_t* __r
 template <int TR, int NW>
 __global__ void __launch_bounds__(NW * 32) k_tile(const __grid_constant__ KArgs a) {
   using G = Geo<TR, NW>;
-  constexpr int TC = G::TC, HC = G::HC, HR = G::HR;
+  constexpr int TC = G::TC;
   extern __shared__ __align__(16) unsigned char smem[];
-  float4* hx = reinterpret_cast<float4*>(smem + G::off_hx);
   int* lp = reinterpret_cast<int*>(smem + G::off_lp);
   uint8_t* tb = smem + G::off_tb;
-  float2* tg = reinterpret_cast<float2*>(smem + G::off_tg);
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  float4* ring = reinterpret_cast<float4*>(smem + G::off_ring) + (size_t)w * (RING + 1) * 32 + lane;
 
   for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
     int lt;
@@ -356,65 +399,31 @@ __global__ void __launch_bounds__(NW * 32) k_tile(const __grid_constant__ KArgs 
     const float4* __restrict__ xyzr = d->xyzr;
     const float* __restrict__ range = d->range;
     const int32_t* __restrict__ order = d->order;
+    const float2* __restrict__ trig = d->trig;
     const float rmin = d->r_min, rmax = d->r_max, jh = d->jump_h, jv = d->jump_v;
 
-    // 1. stage x, y, z, r of the tile and its halo (absent positions r = -1)
-    if (!xyzr) {
-      for (int hc = tid; hc < HC; hc += G::NT) {
-        int j = L.c0 - 1 + hc;
-        if (L.wrap) j = ((j % L.Ws) + L.Ws) % L.Ws;
-        float sp = 0.f, cp = 1.f;
-        sincosf(fmaf((float)(j * L.s), d->daz, d->az0), &sp, &cp);
-        tg[hc] = make_float2(sp, cp);
-      }
-      __syncthreads();
-    }
-    // x,y,z,r input: asynchronous 16-byte copies (cp.async), all of a
-    // thread's copies in flight at once; range input is decoded on the way.
-    for (int k = tid; k < HR * HC; k += G::NT) {
-      const int hr = k / HC, hc = k - (k / HC) * HC;
-      const int i = L.r0 - 1 + hr;
-      int j = L.c0 - 1 + hc;
+    // The sweep: warp w owns tile columns w*29-1 .. w*29+30 (one per lane),
+    // of which lanes 1..29 are its output columns.  Each lane streams its
+    // column's rows from global memory into its own ring of shared-memory
+    // slots with cp.async, RING rows ahead of use (coalesced 16-byte copies
+    // across the warp; a lane only reads slots it filled, so no barrier).  At step hr it holds scan row r0-1+hr and
+    // completes: the R edge of that row, the D and G edges of the row above,
+    // the normal of the row above that (Sec. 2, normal estimation) and the
+    // homogeneity mask of the row above that (Algorithm 1 predicate).
+    {
+      const int col = w * SO + lane;  // tile column + 1
+      const int lc = col - 1;         // tile column
+      const bool out_col = lane >= 1 && lane <= SO && lc < L.cn;
+      int j = L.c0 + lc;              // scan column of this lane
       if (L.wrap) {
         if (j < 0) j += L.Ws;
         else if (j >= L.Ws) j -= L.Ws;
         if (j >= L.Ws) j %= L.Ws;
       }
-      bool present = false;
-      size_t o = 0;
-      if (i >= 0 && i < L.H && j >= 0 && j < L.Ws) {
-        const int row = order[i];
-        if ((unsigned)row < (unsigned)L.H) {
-          o = (size_t)row * L.W + (size_t)j * L.s;
-          present = true;
-        }
-      }
-      if (!present) {
-        hx[k] = make_float4(0.f, 0.f, 0.f, -1.f);
-      } else if (xyzr) {
-        const unsigned dst = (unsigned)__cvta_generic_to_shared(hx + k);
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(xyzr + o) : "memory");
-      } else {
-        const float r = __ldg(range + o);
-        const float2 te = d->trig[i];
-        const float2 ta = tg[hc];
-        const float rc = r * te.y;
-        hx[k] = make_float4(rc * ta.y, rc * ta.x, r * te.x, r);
-      }
-    }
-    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
-    __syncthreads();
-
-    // 2. the sweep: warp w owns staged columns w*29 .. w*29+31 (lanes), of
-    //    which lanes 1..29 are its output columns.  At step hr the warp reads
-    //    staged row hr (scan row r0-1+hr) and completes: the R edge of that
-    //    row, the D and G edges of the row above, the normal of the row above
-    //    that (Sec. 2, normal estimation) and the mask of the row above that
-    //    (Algorithm 1 predicate).
-    {
-      const int col = w * SO + lane;  // staged column
-      const int lc = col - 1;         // tile column
-      const bool out_col = lane >= 1 && lane <= SO && lc < L.cn;
+      const bool colok = j >= 0 && j < L.Ws;
+      const size_t coff = (size_t)(colok ? j : 0) * L.s;
+      float sp = 0.f, cp = 1.f;
+      if (!xyzr && colok) sincosf(fmaf((float)(j * L.s), d->daz, d->az0), &sp, &cp);
       const float nsign = d->nsign, cos_t = d->cos_t;
       const float cx = d->comp_x, cy = d->comp_y, cz = d->comp_z;
       const bool angle_pred = d->pred == LSG_PRED_ANGLE;
@@ -427,9 +436,24 @@ __global__ void __launch_bounds__(NW * 32) k_tile(const __grid_constant__ KArgs 
       float eGx_ppL = 0.f, eGy_ppL = 0.f, eGz_ppL = 0.f, LG_ppL = 0.f;  // G edge of row k-2, left lane
       uint32_t m_pp = 0, m_p = 0;                                // mesh bits of rows k-2, k-1
       float4 n_pp = make_float4(0.f, 0.f, 0.f, 0.f);             // normal of row k-2
+      const int rbase = L.r0 - 1;
+      const int nsteps = L.rn + 3;
+#pragma unroll
+      for (int q = 0; q < RING; ++q) {
+        if (q < nsteps) fetch_point(ring + q * 32, xyzr, range, order, trig, L.H, L.W, rbase + q, colok, coff, sp, cp);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+      }
 
-      for (int hr = 0; hr < HR; ++hr) {
-        const float4 P = hx[hr * HC + col];
+      for (int hr = 0; hr < nsteps; ++hr) {
+        // row hr has landed once at most RING-1 newer groups are pending
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(RING - 1) : "memory");
+        float4 P = ring[(hr % (RING + 1)) * 32];
+        // refill: the slot of row hr+RING was last read one step ago
+        if (hr + RING < nsteps)
+          fetch_point(ring + ((hr + RING) % (RING + 1)) * 32, xyzr, range, order, trig, L.H, L.W, rbase + hr + RING,
+                      colok, coff, sp, cp);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        if (!in_range(P.w, rmin, rmax)) P = make_float4(0.f, 0.f, 0.f, P.w);  // finite spokes only
         float4 Pr;
         Pr.x = __shfl_down_sync(FULL, P.x, 1);
         Pr.y = __shfl_down_sync(FULL, P.y, 1);
@@ -566,7 +590,7 @@ __global__ void __launch_bounds__(NW * 32) k_tile_ccl(const __grid_constant__ KA
 // Scan-local index of the tile-local root of vertex (i, j).
 template <int TR, int TC>
 __device__ __forceinline__ int tile_root(const uint16_t* __restrict__ lroot, int Ws, int i, int j) {
-  const int r = lroot[(size_t)i * Ws + j];
+  const int r = lroot[(size_t)i * root_pitch(Ws) + j];
   const int rr = r / TC, rc = r - (r / TC) * TC;
   return ((i / TR) * TR + rr) * Ws + (j / TC) * TC + rc;
 }
@@ -612,21 +636,22 @@ __global__ void __launch_bounds__(NT_MERGE) k_merge(const __grid_constant__ KArg
       const bool hd_out = (bits & B_HD) && has_down && !down_in;
       const bool hg_out = (bits & B_HG) && has_down && has_right && !(down_in && jn_in);
       if (!(hr_out || hd_out || hg_out)) continue;
-      if (lroot[(size_t)i * L.Ws + j] == NO_ROOT) continue;
+      const size_t LP = root_pitch(L.Ws);
+      if (lroot[(size_t)i * LP + j] == NO_ROOT) continue;
       // along the bottom border, a D edge whose two tile roots equal those of
       // the left neighbour's D edge adds nothing
       if (hd_out && !hr_out && !hg_out && k > 0 && k < L.cn) {
         const uint8_t bl = mb[(size_t)i * L.Ws + j - 1];
-        if ((bl & B_HD) && lroot[(size_t)i * L.Ws + j - 1] == lroot[(size_t)i * L.Ws + j] &&
-            lroot[(size_t)(i + 1) * L.Ws + j - 1] == lroot[(size_t)(i + 1) * L.Ws + j])
+        if ((bl & B_HD) && lroot[(size_t)i * LP + j - 1] == lroot[(size_t)i * LP + j] &&
+            lroot[(size_t)(i + 1) * LP + j - 1] == lroot[(size_t)(i + 1) * LP + j])
           continue;
       }
       const int rp = tile_root<TR, TC>(lroot, L.Ws, i, j);
-      if (hr_out && lroot[(size_t)i * L.Ws + jn] != NO_ROOT)
+      if (hr_out && lroot[(size_t)i * LP + jn] != NO_ROOT)
         union_g(parent, rp, tile_root<TR, TC>(lroot, L.Ws, i, jn), limit, a.err);
-      if (hd_out && lroot[(size_t)(i + 1) * L.Ws + j] != NO_ROOT)
+      if (hd_out && lroot[(size_t)(i + 1) * LP + j] != NO_ROOT)
         union_g(parent, rp, tile_root<TR, TC>(lroot, L.Ws, i + 1, j), limit, a.err);
-      if (hg_out && lroot[(size_t)(i + 1) * L.Ws + jn] != NO_ROOT)
+      if (hg_out && lroot[(size_t)(i + 1) * LP + jn] != NO_ROOT)
         union_g(parent, rp, tile_root<TR, TC>(lroot, L.Ws, i + 1, jn), limit, a.err);
     }
   }
@@ -653,7 +678,7 @@ template <int TR, int TC>
 __device__ __forceinline__ int32_t vertex_label_global(const uint16_t* __restrict__ lroot,
                                                        const int32_t* __restrict__ parent, int Ws, int W,
                                                        int s, int i, int j, int limit) {
-  if (lroot[(size_t)i * Ws + j] == NO_ROOT) return -1;
+  if (lroot[(size_t)i * root_pitch(Ws) + j] == NO_ROOT) return -1;
   const int g = find_ro(parent, tile_root<TR, TC>(lroot, Ws, i, j), limit);
   const int gi = g / Ws, gj = g - gi * Ws;
   return gi * W + gj * s;
@@ -677,10 +702,23 @@ __device__ __forceinline__ int32_t backfill(int32_t lo, int dlo, int32_t hi, int
 // between sampled columns.  Loops are two-dimensional (warps over rows,
 // lanes over columns): no integer division per point.
 template <int TR, int NW>
+struct FlatGeo {
+  static constexpr int TC = NW * SO, NV = TR * TC;
+  static constexpr size_t off_lr = 0;                                      // uint16 [NV] tile roots
+  static constexpr size_t off_lab = ((sizeof(uint16_t) * NV + 15) / 16) * 16;  // int32 [NV] root labels
+  static constexpr size_t off_list = off_lab + sizeof(int32_t) * NV;       // uint16 [NV] list of roots
+  static constexpr size_t bytes = off_list + ((sizeof(uint16_t) * NV + 15) / 16) * 16;
+};
+
+template <int TR, int NW>
 __global__ void __launch_bounds__(NT_FLAT) k_flatten(const __grid_constant__ KArgs a) {
-  constexpr int TC = NW * SO, NV = TR * TC, NWF = NT_FLAT / 32;
-  __shared__ uint16_t lr_s[NV];
-  __shared__ int32_t lab_s[NV];
+  using FG = FlatGeo<TR, NW>;
+  constexpr int TC = FG::TC, NWF = NT_FLAT / 32;
+  extern __shared__ __align__(16) unsigned char fsm[];
+  uint16_t* lr_s = reinterpret_cast<uint16_t*>(fsm + FG::off_lr);
+  int32_t* lab_s = reinterpret_cast<int32_t*>(fsm + FG::off_lab);
+  uint16_t* list_s = reinterpret_cast<uint16_t*>(fsm + FG::off_list);
+  __shared__ int nlist;
   const int tid = threadIdx.x, lane = tid & 31, wf = tid >> 5;
   for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
     int lt;
@@ -691,23 +729,66 @@ __global__ void __launch_bounds__(NT_FLAT) k_flatten(const __grid_constant__ KAr
     const int32_t* __restrict__ parent = d->parent;
     int32_t* __restrict__ labels = d->labels;
     const int limit = L.H * Ws + 1;
+    if (tid == 0) nlist = 0;
+    // (1) the tile's roots, four at a time (rows are 8-byte aligned: the
+    //     pitch is a multiple of 8 and TC a multiple of 4)
+    const int nq = (L.cn + 3) >> 2;
     for (int lr = wf; lr < L.rn; lr += NWF) {
-      const uint16_t* src = lroot + (size_t)(L.r0 + lr) * Ws + L.c0;
-#pragma unroll 4
-      for (int lc = lane; lc < L.cn; lc += 32) lr_s[lr * TC + lc] = src[lc];
+      const uint2* src = reinterpret_cast<const uint2*>(lroot + (size_t)(L.r0 + lr) * root_pitch(Ws) + L.c0);
+      uint2* dst = reinterpret_cast<uint2*>(lr_s + lr * TC);
+#pragma unroll 2
+      for (int q = lane; q < nq; q += 32) dst[q] = __ldg(src + q);
+    }
+    __syncthreads();
+    // (2) list the tile-local roots, then resolve each to its global root,
+    //     four chains per thread at a time
+    for (int lr = wf; lr < L.rn; lr += NWF) {
+      for (int lc0 = 0; lc0 < L.cn; lc0 += 32) {
+        const int lc = lc0 + lane;
+        const int v = lr * TC + lc;
+        const bool is_root = lc < L.cn && lr_s[v] == v;
+        const unsigned m = __ballot_sync(FULL, is_root);
+        int base = 0;
+        if (lane == 0 && m) base = atomicAdd(&nlist, __popc(m));
+        base = __shfl_sync(FULL, base, 0);
+        if (is_root) list_s[base + __popc(m & ((1u << lane) - 1u))] = (uint16_t)v;
+      }
     }
     __syncthreads();
     int nroots = 0;
-    for (int lr = wf; lr < L.rn; lr += NWF) {
-      for (int lc = lane; lc < L.cn; lc += 32) {
-        const int v = lr * TC + lc;
-        if (lr_s[v] == v) {  // a tile-local root
-          const int gv = (L.r0 + lr) * Ws + L.c0 + lc;
-          const int g = find_ro(parent, gv, limit);
-          nroots += (g == gv);
-          const int gi = g / Ws, gj = g - gi * Ws;
-          lab_s[v] = gi * W + gj * s;
+    const int nl = nlist;
+    for (int k0 = tid; k0 < nl; k0 += 4 * NT_FLAT) {
+      int x[4], gv[4];
+      bool live[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int k = k0 + q * NT_FLAT;
+        live[q] = k < nl;
+        const int v = live[q] ? list_s[k] : 0;
+        gv[q] = (L.r0 + v / TC) * Ws + L.c0 + v % TC;
+        x[q] = gv[q];
+      }
+      // walk the four chains together (independent loads in flight)
+      for (int it = 0; it < limit; ++it) {
+        bool more = false;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (!live[q]) continue;
+          const int p = __ldg(parent + x[q]);
+          if (p != x[q]) {
+            x[q] = p;
+            more = true;
+          }
         }
+        if (!more) break;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (!live[q]) continue;
+        const int g = x[q];
+        nroots += (g == gv[q]);
+        const int gi = g / Ws, gj = g - gi * Ws;
+        lab_s[list_s[k0 + q * NT_FLAT]] = gi * W + gj * s;
       }
     }
     const int cnt = __reduce_add_sync(FULL, nroots);
@@ -779,6 +860,9 @@ static cudaError_t set_attrs() {
   cudaError_t e = cudaFuncSetAttribute(k_tile<TR, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)Geo<TR, NW>::bytes);
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_flatten<TR, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)FlatGeo<TR, NW>::bytes);
+  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_tile_ccl<TR, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)Geo<TR, NW>::ccl_bytes);
 }
@@ -787,9 +871,9 @@ cudaError_t prepare_kernels() {
   cudaError_t e;
   if ((e = set_attrs<16, 4>()) != cudaSuccess) return e;
   if ((e = set_attrs<32, 4>()) != cudaSuccess) return e;
-  if ((e = set_attrs<8, 8>()) != cudaSuccess) return e;
-  if ((e = set_attrs<16, 8>()) != cudaSuccess) return e;
   if ((e = set_attrs<32, 8>()) != cudaSuccess) return e;
+  if ((e = set_attrs<64, 4>()) != cudaSuccess) return e;
+  if ((e = set_attrs<64, 8>()) != cudaSuccess) return e;
   return cudaSuccess;
 }
 
@@ -802,9 +886,9 @@ cudaError_t launch_prep(const KArgs& a, cudaStream_t st) {
 #define LSG_DISPATCH(tile, FN, ...)                       \
   switch (tile) {                                         \
     case LSG_TILE_32x116: return FN<32, 4>(__VA_ARGS__);  \
-    case LSG_TILE_8x232: return FN<8, 8>(__VA_ARGS__);    \
-    case LSG_TILE_16x232: return FN<16, 8>(__VA_ARGS__);  \
     case LSG_TILE_32x232: return FN<32, 8>(__VA_ARGS__);  \
+    case LSG_TILE_64x116: return FN<64, 4>(__VA_ARGS__);  \
+    case LSG_TILE_64x232: return FN<64, 8>(__VA_ARGS__);  \
     default: return FN<16, 4>(__VA_ARGS__);               \
   }
 
@@ -825,7 +909,7 @@ static cudaError_t run_merge(const KArgs& a, cudaStream_t st) {
 }
 template <int TR, int NW>
 static cudaError_t run_flatten(const KArgs& a, cudaStream_t st) {
-  k_flatten<TR, NW><<<a.ntiles, NT_FLAT, 0, st>>>(a);
+  k_flatten<TR, NW><<<a.ntiles, NT_FLAT, FlatGeo<TR, NW>::bytes, st>>>(a);
   return cudaGetLastError();
 }
 

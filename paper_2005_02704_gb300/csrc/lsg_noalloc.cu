@@ -31,7 +31,8 @@ constexpr size_t kTrigOff = kOrderOff + sizeof(int32_t) * LSG_MAX_RINGS;  // flo
 constexpr size_t kErrOff = kTrigOff + sizeof(float2) * LSG_MAX_RINGS;     // int32 error word
 constexpr size_t kParentOff = kErrOff + 256;                             // int32[max vertices]
 constexpr size_t kRootOff = kParentOff + sizeof(int32_t) * (size_t)LSG_NOALLOC_MAX_VERTICES;  // uint16[max]
-constexpr size_t kScratchBytes = kRootOff + sizeof(uint16_t) * (size_t)LSG_NOALLOC_MAX_VERTICES;
+// tile-root rows are padded to 8 entries: at most 7 extra per ring
+constexpr size_t kScratchBytes = kRootOff + sizeof(uint16_t) * ((size_t)LSG_NOALLOC_MAX_VERTICES + 8 * LSG_MAX_RINGS);
 static_assert(kTrigOff % 256 == 0 && kErrOff % 256 == 0 && kParentOff % 256 == 0 && kRootOff % 256 == 0,
               "alignment");
 

@@ -20,7 +20,7 @@ from . import _build
 LSG_OK, LSG_E_ARG, LSG_E_SHAPE, LSG_E_OOM, LSG_E_BUDGET, LSG_E_CUDA, LSG_E_TIMEOUT, LSG_E_DEVICE = range(8)
 LSG_PRED_ANGLE, LSG_PRED_COMPONENT = 0, 1
 LSG_TILE_AUTO = -1
-TILES = {"16x116": 0, "32x116": 1, "8x232": 2, "16x232": 3, "32x232": 4}
+TILES = {"16x116": 0, "32x116": 1, "32x232": 2, "64x116": 3, "64x232": 4}
 LSG_TILE_COUNT = len(TILES)
 
 BIT_R, BIT_D, BIT_G = 0x01, 0x02, 0x04
@@ -181,7 +181,7 @@ def lsg_reserve(ctx: int, workspace_bytes: int, max_scans: int, max_tiles: int) 
 def scan_workspace_bytes(H: int, Ws: int) -> int:
     """Workspace of one scan inside a batch (four arrays, 256-byte aligned)."""
     up = lambda x: (x + 255) // 256 * 256
-    return up(4 * H) + up(8 * H) + up(4 * H * Ws) + up(2 * H * Ws)
+    return up(4 * H) + up(8 * H) + up(4 * H * Ws) + up(2 * H * ((Ws + 7) & ~7))
 
 
 def lsg_autotune(plan: int, reps: int = 3, stream: int = 0):

@@ -39,7 +39,7 @@ def slot_bytes(key: ShapeKey) -> int:
     Ws = lsg.ws_of(W, s)
     inputs = H * W * 16 + H * 4
     outputs = H * Ws * (1 + 12) + H * W * 4 + 4
-    workspace = H * 12 + H * Ws * 6
+    workspace = H * 12 + H * Ws * 4 + H * ((Ws + 7) & ~7) * 2
     return inputs + outputs + workspace
 
 

@@ -55,7 +55,7 @@ def mixed_specs(n, seed0):
     return specs
 
 
-@pytest.mark.parametrize("tile", ["16x116", "32x116", "8x232", "16x232", "32x232"])
+@pytest.mark.parametrize("tile", ["16x116", "32x116", "32x232", "64x116", "64x232"])
 def test_batch_equals_per_scan(ctx, tile):
     lsg, _ = mods()
     specs = mixed_specs(12, 5000)

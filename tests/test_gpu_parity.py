@@ -111,10 +111,10 @@ def test_component_predicate(ctx):
 
 RAGGED = [
     # (rings, cols, s, wrap, tile)
-    (1, 1, 1, 1, "16x116"), (1, 7, 1, 1, "16x116"), (2, 2, 1, 1, "16x116"), (3, 3, 1, 1, "32x232"),
-    (9, 131, 1, 1, "16x116"), (9, 131, 1, 0, "16x116"), (17, 257, 2, 1, "8x232"), (17, 257, 3, 0, "32x116"),
-    (5, 1030, 1, 1, "16x232"), (33, 129, 1, 1, "32x232"), (16, 1800, 5, 1, "16x116"), (7, 1000, 15, 1, "8x232"),
-    (64, 300, 1, 1, "32x116"), (3, 512, 2, 1, "16x232"), (24, 640, 4, 0, "32x232"),
+    (1, 1, 1, 1, "16x116"), (1, 7, 1, 1, "16x116"), (2, 2, 1, 1, "16x116"), (3, 3, 1, 1, "64x232"),
+    (9, 131, 1, 1, "16x116"), (9, 131, 1, 0, "16x116"), (17, 257, 2, 1, "32x232"), (17, 257, 3, 0, "32x116"),
+    (5, 1030, 1, 1, "64x116"), (33, 129, 1, 1, "64x232"), (16, 1800, 5, 1, "16x116"), (7, 1000, 15, 1, "32x232"),
+    (64, 300, 1, 1, "32x116"), (3, 512, 2, 1, "64x116"), (24, 640, 4, 0, "64x232"),
 ]
 
 
@@ -194,7 +194,7 @@ def test_label_from_mask_random_masks(ctx):
             flat[hom] |= hb
         mb = flat.reshape(H, Ws)
         want, nwant = O.label_from_mask(mb, valid_full, W, s, wrap)
-        for tile in ("16x116", "16x232", "8x232"):
+        for tile in ("16x116", "64x116", "32x232"):
             lsg.lsg_set_tile(ctx.h, lsg.TILES[tile])
             got, n = ctx.label_from_mask(torch.from_numpy(mb).to(dev), torch.from_numpy(valid_full).to(dev), W, s,
                                          wrap)

@@ -50,6 +50,7 @@ def test_oversized_scan_is_refused():
 def test_slot_bytes_counts_inputs_outputs_and_workspace():
     H, W, s = 128, 4096, 1
     assert serve.slot_bytes((H, W, s)) == H * W * 16 + H * 4 + H * W * 13 + H * W * 4 + 4 + H * 12 + H * W * 6
+    assert serve.slot_bytes((3, 5, 1)) == 3 * 5 * 16 + 3 * 4 + 3 * 5 * 17 + 4 + 3 * 12 + 3 * 5 * 4 + 3 * 8 * 2
     assert serve.slot_bytes((64, 2048, 2)) < serve.slot_bytes((64, 2048, 1))
 
 
