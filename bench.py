@@ -62,6 +62,9 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--phased", action="store_true", help="force four phased launches (else the autotuner's choice)")
+    ap.add_argument("--fused", action="store_true", help="force the single persistent launch")
+    ap.add_argument("--tile", default=None, help="force a tile shape (e.g. 32x116) instead of autotuning")
     ap.add_argument("--serve-scale", type=float, default=10.0,
                     help="time compression of the 60 s sensor trace for the served measurement")
     return ap.parse_args()
@@ -141,11 +144,11 @@ def measured_hbm():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def profiled_traffic():
-    """DRAM bytes per point of the tile kernel from the committed ncu summary,
+def profiled_traffic(kernel: str):
+    """DRAM bytes per point of the kernel from its committed ncu summary,
     valid only while the kernel source is unchanged since the capture."""
     src = os.path.join(ROOT, "paper_2005_02704_gb300", "csrc", "lsg_kernels.cu")
-    prof = os.path.join(ROOT, "profiles", "k_tile_batch512.md")
+    prof = os.path.join(ROOT, "profiles", f"{kernel}_batch512.md")
     try:
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
         vals = {}
@@ -307,11 +310,15 @@ def main():
     db.upload()
     torch.cuda.synchronize()
     ctx = lsg.Context(local)
-    plan = db.plan(ctx)
+    plan = db.plan(ctx, lsg.TILES[args.tile] if args.tile else lsg.LSG_TILE_AUTO)
     stream = torch.cuda.current_stream()
     tuned = None
-    if not args.no_autotune:
+    if not args.no_autotune and not args.tile:
         tuned = plan.autotune(reps=3)
+    if args.phased:
+        plan.set_fused(False)
+    if args.fused:
+        plan.set_fused(True)
     tile_name = {v: k for k, v in lsg.TILES.items()}[plan.tile]
 
     # ---- batched path, inputs resident ------------------------------------
@@ -400,14 +407,21 @@ def main():
         served = serve_measurement(args, local, world, max_over_ranks, sum_over_ranks)
 
     # ---- roofline of the dominant kernel ---------------------------------
+    # the fused plan runs the whole pass in one persistent launch (k_fused),
+    # whose algorithmic bytes are the path's; the phased plan's dominant
+    # kernel is the tile kernel
     peak, peak_kind = measured_hbm()
-    t_tile = phase[1] / 1e3
-    achieved = TILE_BYTES_PER_POINT * db.points / t_tile / 1e9
-    traffic_pp = profiled_traffic()
-    roof = {"bound": "hbm", "kernel": "k_tile (decode+mesh+normals+edge mask+tile components)",
+    t_dom = phase[1] / 1e3
+    fused = plan.fused
+    bpp = PATH_BYTES_PER_POINT if fused else TILE_BYTES_PER_POINT
+    achieved = bpp * db.points / t_dom / 1e9
+    traffic_pp = profiled_traffic("k_fused" if fused else "k_tile")
+    roof = {"bound": "hbm",
+            "kernel": ("k_fused (the whole pass in one persistent launch)" if fused else
+                       "k_tile (decode+mesh+normals+edge mask+tile components)"),
             "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "peak_source": f"{peak_kind} HBM copy bandwidth",
-            "algorithmic_bytes_per_launch": TILE_BYTES_PER_POINT * db.points,
+            "algorithmic_bytes_per_launch": bpp * db.points,
             "traffic": (traffic_pp * db.points) if traffic_pp is not None else None}
     path_achieved = PATH_BYTES_PER_POINT * db.points / (ms_step / 1e3) / 1e9
 
@@ -428,21 +442,23 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "scans_per_gpu": db.n, "points_per_gpu": db.points,
-                       "tile": tile_name, "autotune_ms": tuned[1] if tuned else None,
+                       "tile": tile_name, "schedule": "fused (one persistent launch)" if fused else "phased (4 launches)",
+                       "autotune_ms": tuned[1] if tuned else None,
                        "l2": "inputs larger than L2 (x,y,z,r %.2f GB per GPU > 129 MB), no flush" % (
                            db.points * 16 / 1e9),
                        "parallelism": f"replicas x{world}"},
             "roofline": roof,
             "path_roofline": {"bound": "hbm", "achieved": path_achieved, "peak": peak, "unit": "GB/s",
                               "frac": path_achieved / peak, "bytes_per_point": PATH_BYTES_PER_POINT},
-            "kernel_ms": {"ring_order": phase[0], "tile": phase[1], "merge": phase[2], "labels": phase[3]},
+            "kernel_ms": ({"counter_reset": phase[0], "fused": phase[1]} if fused else
+                          {"ring_order": phase[0], "tile": phase[1], "merge": phase[2], "labels": phase[3]}),
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": ms_e2e},
             "plain": plain,
             "served": served,
             "scans_per_s": db.n * world / (ms_step / 1e3),
-            "gpu_launches": 4 * args.steps,
+            "gpu_launches": (1 if fused else 4) * args.steps,
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)

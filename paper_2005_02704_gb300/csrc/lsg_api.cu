@@ -7,6 +7,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -48,6 +49,10 @@ struct lsg_plan {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // phase boundaries
+  int fused = 1;                    // one persistent launch (1) or four phased launches (0)
+  int2* d_items = nullptr;          // fused schedule
+  int32_t nitems = 0;
+  int32_t* d_counters = nullptr;    // [1 + 3n] fused progress counters
 };
 
 namespace {
@@ -513,6 +518,48 @@ static lsg_status plan_layout(lsg_plan* pl, int tile) {
     if (e == cudaSuccess)
       e = cudaMemcpy(pl->d_tile_scan, ts.data(), sizeof(int32_t) * t0, cudaMemcpyHostToDevice);
   }
+  // fused schedule: every scan's ring order first, then the tiles of all
+  // scans in order, with a scan's border merges placed LAG items after its
+  // last tile and its labels LAG items after its last merge.  LAG exceeds the
+  // number of CTAs that run at once, so an item rarely finds its inputs
+  // unfinished, while a scan's labels still follow its tiles closely enough
+  // for their data to be in L2.
+  const size_t LAG = 2048;
+  std::vector<int2> items;
+  items.reserve(pl->n + 3 * (size_t)t0);
+  for (int b = 0; b < pl->n; ++b) items.push_back(make_int2(PH_PREP << 28 | b, 0));
+  struct Due {
+    size_t at;
+    int ph, b;
+  };
+  std::vector<Due> due;  // FIFO, `at` non-decreasing per phase
+  size_t head = 0;
+  auto tiles_of = [&](int b) {
+    const ScanDesc& d = pl->host_desc[b];
+    return (d.H && d.W) ? d.tiles_r * d.tiles_c : 0;
+  };
+  auto emit_due = [&](bool all) {
+    while (head < due.size() && (all || due[head].at <= items.size())) {
+      const Due x = due[head++];
+      for (int k = 0; k < tiles_of(x.b); ++k) items.push_back(make_int2(x.ph << 28 | x.b, k));
+      if (x.ph == PH_MERGE) due.push_back(Due{items.size() + LAG, PH_FLAT, x.b});
+    }
+  };
+  for (int b = 0; b < pl->n; ++b) {
+    for (int k = 0; k < tiles_of(b); ++k) {
+      emit_due(false);
+      items.push_back(make_int2(PH_TILE << 28 | b, k));
+    }
+    if (tiles_of(b) > 0) due.push_back(Due{items.size() + LAG, PH_MERGE, b});
+  }
+  emit_due(true);
+  pl->nitems = (int32_t)items.size();
+  if (pl->d_items) cudaFree(pl->d_items);
+  pl->d_items = nullptr;
+  if (e == cudaSuccess) e = cudaMalloc(&pl->d_items, sizeof(int2) * items.size());
+  if (e == cudaSuccess)
+    e = cudaMemcpy(pl->d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !pl->d_counters) e = cudaMalloc(&pl->d_counters, sizeof(int32_t) * (1 + 3 * (size_t)pl->n));
   if (e == cudaSuccess)
     e = cudaMemcpy(pl->d_desc, pl->host_desc.data(), sizeof(ScanDesc) * pl->n, cudaMemcpyHostToDevice);
   pl->tile = tile;
@@ -543,14 +590,31 @@ static lsg_status plan_capture(lsg_plan* pl) {
     // runs one block per scan); the tile kernels see only non-empty scans.
     // Event-record nodes between the phases give per-kernel device times.
     cudaError_t le = cudaEventRecordWithFlags(pl->ev[0], cs, cudaEventRecordExternal);
-    if (le == cudaSuccess) le = launch_prep(a, cs);
-    if (le == cudaSuccess) le = cudaEventRecordWithFlags(pl->ev[1], cs, cudaEventRecordExternal);
-    if (le == cudaSuccess && pl->ntiles > 0) le = launch_tile(pl->tile, a, cs);
-    if (le == cudaSuccess) le = cudaEventRecordWithFlags(pl->ev[2], cs, cudaEventRecordExternal);
-    if (le == cudaSuccess && pl->ntiles > 0) le = launch_merge(pl->tile, a, cs);
-    if (le == cudaSuccess) le = cudaEventRecordWithFlags(pl->ev[3], cs, cudaEventRecordExternal);
-    if (le == cudaSuccess && pl->ntiles > 0) le = launch_flatten(pl->tile, a, cs);
-    if (le == cudaSuccess) le = cudaEventRecordWithFlags(pl->ev[4], cs, cudaEventRecordExternal);
+    if (pl->fused) {
+      // counters reset, then the single persistent launch
+      FusedArgs f;
+      f.scans = pl->d_desc;
+      f.items = pl->d_items;
+      f.nitems = pl->nitems;
+      f.nscans = pl->n;
+      f.counters = pl->d_counters;
+      f.err = pl->ctx->d_err;
+      if (le == cudaSuccess) le = cudaMemsetAsync(pl->d_counters, 0, sizeof(int32_t) * (1 + 3 * (size_t)pl->n), cs);
+      if (le == cudaSuccess) le = cudaEventRecordWithFlags(pl->ev[1], cs, cudaEventRecordExternal);
+      if (le == cudaSuccess) le = launch_fused(pl->tile, f, cs);
+      if (le == cudaSuccess) le = cudaEventRecordWithFlags(pl->ev[2], cs, cudaEventRecordExternal);
+      if (le == cudaSuccess) le = cudaEventRecordWithFlags(pl->ev[3], cs, cudaEventRecordExternal);
+      if (le == cudaSuccess) le = cudaEventRecordWithFlags(pl->ev[4], cs, cudaEventRecordExternal);
+    } else {
+      if (le == cudaSuccess) le = launch_prep(a, cs);
+      if (le == cudaSuccess) le = cudaEventRecordWithFlags(pl->ev[1], cs, cudaEventRecordExternal);
+      if (le == cudaSuccess && pl->ntiles > 0) le = launch_tile(pl->tile, a, cs);
+      if (le == cudaSuccess) le = cudaEventRecordWithFlags(pl->ev[2], cs, cudaEventRecordExternal);
+      if (le == cudaSuccess && pl->ntiles > 0) le = launch_merge(pl->tile, a, cs);
+      if (le == cudaSuccess) le = cudaEventRecordWithFlags(pl->ev[3], cs, cudaEventRecordExternal);
+      if (le == cudaSuccess && pl->ntiles > 0) le = launch_flatten(pl->tile, a, cs);
+      if (le == cudaSuccess) le = cudaEventRecordWithFlags(pl->ev[4], cs, cudaEventRecordExternal);
+    }
     e = cudaStreamEndCapture(cs, &pl->graph);
     if (le != cudaSuccess) e = le;
   }
@@ -577,7 +641,9 @@ lsg_status lsg_batch_plan(lsg_ctx* ctx, int32_t n, const lsg_scan* scans, const 
   size_t tiles_max = 0;
   for (int b = 0; b < n; ++b)
     tiles_max += (size_t)(scans[b].rings / 16 + 1) * (Ws[b] / 116 + 1);
-  const size_t bytes = ws_total + align_up(sizeof(ScanDesc) * n, 256) + sizeof(int32_t) * tiles_max;
+  // workspace, descriptors, tile table, fused schedule (scan + 3 items per tile) and counters
+  const size_t bytes = ws_total + align_up(sizeof(ScanDesc) * n, 256) + sizeof(int32_t) * tiles_max +
+                       sizeof(int2) * (n + 3 * tiles_max) + sizeof(int32_t) * (1 + 3 * (size_t)n);
   if (ctx->budget && ctx->used + bytes > ctx->budget) return LSG_E_BUDGET;
   DeviceGuard g(ctx->device);
   lsg_plan* pl = new (std::nothrow) lsg_plan();
@@ -619,6 +685,13 @@ lsg_status lsg_batch_run(lsg_plan* plan, lsg_stream stream) {
 
 int lsg_plan_tile(const lsg_plan* plan) { return plan ? plan->tile : -1; }
 
+lsg_status lsg_plan_set_fused(lsg_plan* plan, int fused) {
+  if (!plan) return LSG_E_ARG;
+  DeviceGuard g(plan->ctx->device);
+  plan->fused = fused ? 1 : 0;
+  return plan_capture(plan);
+}
+
 lsg_status lsg_plan_phase_times(lsg_plan* plan, float* ms) {
   if (!plan || !ms || !plan->ev[4]) return LSG_E_ARG;
   DeviceGuard g(plan->ctx->device);
@@ -637,38 +710,46 @@ lsg_status lsg_autotune(lsg_plan* plan, int reps, lsg_stream stream, int* best_t
     cudaEventDestroy(e0);
     return LSG_E_CUDA;
   }
-  int best = plan->tile;
+  int best = plan->tile, best_fused = plan->fused;
   float best_t = INFINITY;
   lsg_status st = LSG_OK;
-  for (int t = 0; t < LSG_TILE_COUNT && st == LSG_OK; ++t) {
-    st = plan_layout(plan, t);
-    if (st == LSG_OK) st = plan_capture(plan);
-    if (st != LSG_OK) break;
-    cudaGraphLaunch(plan->exec, cs);  // warm-up
-    cudaEventRecord(e0, cs);
-    for (int r = 0; r < reps; ++r) cudaGraphLaunch(plan->exec, cs);
-    cudaEventRecord(e1, cs);
-    cudaError_t e = cudaEventSynchronize(e1);
-    if (e != cudaSuccess) {
-      st = cuda_status(e);
-      break;
-    }
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    ms /= reps;
-    if (ms < best_t) {
-      best_t = ms;
-      best = t;
+  // every tile shape under both schedules (one persistent launch, or four)
+  for (int fused = 1; fused >= 0 && st == LSG_OK; --fused) {
+    for (int t = 0; t < LSG_TILE_COUNT && st == LSG_OK; ++t) {
+      plan->fused = fused;
+      st = plan_layout(plan, t);
+      if (st == LSG_OK) st = plan_capture(plan);
+      if (st != LSG_OK) break;
+      cudaGraphLaunch(plan->exec, cs);  // warm-up
+      cudaEventRecord(e0, cs);
+      for (int r = 0; r < reps; ++r) cudaGraphLaunch(plan->exec, cs);
+      cudaEventRecord(e1, cs);
+      cudaError_t e = cudaEventSynchronize(e1);
+      if (e != cudaSuccess) {
+        st = cuda_status(e);
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms /= reps;
+      if (ms < best_t) {
+        best_t = ms;
+        best = t;
+        best_fused = fused;
+      }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  plan->fused = best_fused;
   if (st == LSG_OK) st = plan_layout(plan, best);
   if (st == LSG_OK) st = plan_capture(plan);
   if (best_tile) *best_tile = best;
   if (best_ms) *best_ms = best_t;
   return st;
 }
+
+int lsg_plan_fused(const lsg_plan* plan) { return plan ? plan->fused : -1; }
 
 lsg_status lsg_plan_destroy(lsg_plan* plan) {
   if (!plan) return LSG_E_ARG;
@@ -679,6 +760,8 @@ lsg_status lsg_plan_destroy(lsg_plan* plan) {
   for (int k = 0; k < 5; ++k)
     if (plan->ev[k]) cudaEventDestroy(plan->ev[k]);
   if (plan->d_tile_scan) cudaFree(plan->d_tile_scan);
+  if (plan->d_items) cudaFree(plan->d_items);
+  if (plan->d_counters) cudaFree(plan->d_counters);
   if (plan->d_desc) cudaFree(plan->d_desc);
   if (plan->ws) cudaFree(plan->ws);
   plan->ctx->used -= plan->bytes;

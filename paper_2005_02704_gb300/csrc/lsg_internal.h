@@ -46,6 +46,20 @@ struct KArgs {
   ScanDesc one;
 };
 
+// The persistent fused pass: one launch that walks a schedule of work items
+// (ring order of a scan, then its tiles, border merges and labels), each item
+// waiting only on items scheduled before it.
+enum : int32_t { PH_PREP = 0, PH_TILE = 1, PH_MERGE = 2, PH_FLAT = 3 };
+
+struct FusedArgs {
+  const ScanDesc* scans;  // device table
+  const int2* items;      // [nitems] (phase << 28 | scan, local tile)
+  int32_t nitems;
+  int32_t nscans;
+  int32_t* counters;      // [0] next item, then per scan: rings done, tiles done, merges done
+  int32_t* err;
+};
+
 // Device error codes (sticky, OR-ed into *err).
 enum : int32_t { DERR_NAN_ELEV = 1, DERR_TIMEOUT = 2 };
 
@@ -65,6 +79,7 @@ cudaError_t launch_tile(int tile, const KArgs& a, cudaStream_t st);
 cudaError_t launch_tile_ccl(int tile, const KArgs& a, cudaStream_t st);
 cudaError_t launch_merge(int tile, const KArgs& a, cudaStream_t st);
 cudaError_t launch_flatten(int tile, const KArgs& a, cudaStream_t st);
+cudaError_t launch_fused(int tile, const FusedArgs& f, cudaStream_t st);
 cudaError_t prepare_kernels();  // one-time function attributes
 
 }  // namespace lsg

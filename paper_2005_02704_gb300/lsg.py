@@ -86,6 +86,8 @@ def load(build: bool = True):
             "lsg_autotune": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_int),
                                             ctypes.POINTER(ctypes.c_float)]),
             "lsg_plan_tile": (ctypes.c_int, [_P]),
+            "lsg_plan_set_fused": (ctypes.c_int, [_P, ctypes.c_int]),
+            "lsg_plan_fused": (ctypes.c_int, [_P]),
             "lsg_plan_phase_times": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float)]),
             "lsg_plan_destroy": (ctypes.c_int, [_P]),
             "lsg_get_error": (ctypes.c_int, [_P]),
@@ -193,6 +195,10 @@ def lsg_autotune(plan: int, reps: int = 3, stream: int = 0):
 
 def lsg_plan_tile(plan: int) -> int:
     return load().lsg_plan_tile(plan)
+
+
+def lsg_plan_set_fused(plan: int, fused: bool) -> None:
+    _check(load().lsg_plan_set_fused(plan, 1 if fused else 0), "lsg_plan_set_fused")
 
 
 def lsg_plan_phase_times(plan: int):
@@ -366,6 +372,13 @@ class BatchPlan:
     @property
     def tile(self) -> int:
         return lsg_plan_tile(self.h)
+
+    def set_fused(self, fused: bool):
+        lsg_plan_set_fused(self.h, fused)
+
+    @property
+    def fused(self) -> bool:
+        return load().lsg_plan_fused(self.h) == 1
 
     def phase_times(self):
         """[ring order, tile kernel, border merge, labels] ms of the last replay."""

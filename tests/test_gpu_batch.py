@@ -55,13 +55,15 @@ def mixed_specs(n, seed0):
     return specs
 
 
+@pytest.mark.parametrize("fused", [True, False], ids=["fused", "phased"])
 @pytest.mark.parametrize("tile", ["16x116", "32x116", "32x232", "64x116", "64x232"])
-def test_batch_equals_per_scan(ctx, tile):
+def test_batch_equals_per_scan(ctx, tile, fused):
     lsg, _ = mods()
     specs = mixed_specs(12, 5000)
     scans = [lidarsim.make_scan(sp) for sp in specs]
     db = make_batch(specs, scans)
     plan = db.plan(ctx, lsg.TILES[tile])
+    plan.set_fused(fused)
     plan.run()
     plan.run()  # replays are idempotent
     torch.cuda.synchronize()
