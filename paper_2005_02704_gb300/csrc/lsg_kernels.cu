@@ -94,11 +94,13 @@ __device__ __forceinline__ void tri_term(float ax, float ay, float az, float la,
 
 // Homogeneity predicate of Algorithm 1 between two vertices' normals
 // (w = 1 when the vertex has a normal).
+// Branch-free: both forms are evaluated and the predicate selects one.
 __device__ __forceinline__ bool homog(const float4 u, const float4 v, bool angle_pred, float cos_t, float cx,
                                       float cy, float cz) {
-  if (u.w == 0.f || v.w == 0.f) return false;
-  if (angle_pred) return fmaf(u.x, v.x, fmaf(u.y, v.y, u.z * v.z)) > cos_t;
-  return fabsf(u.x - v.x) < cx && fabsf(u.y - v.y) < cy && fabsf(u.z - v.z) < cz;
+  const bool both = (u.w != 0.f) & (v.w != 0.f);
+  const bool by_angle = fmaf(u.x, v.x, fmaf(u.y, v.y, u.z * v.z)) > cos_t;
+  const bool by_comp = (fabsf(u.x - v.x) < cx) & (fabsf(u.y - v.y) < cy) & (fabsf(u.z - v.z) < cz);
+  return both & (angle_pred ? by_angle : by_comp);
 }
 
 __device__ __forceinline__ const ScanDesc* tile_desc(const KArgs& a, int t, int& lt) {
@@ -234,31 +236,29 @@ struct Geo {
   static constexpr size_t off_ring = 0;          // per-warp row rings [NW][RING+1][32] float4
   static constexpr size_t off_lp = off_ring + sizeof(float4) * NW * (RING + 1) * 32;  // tile union-find
   static constexpr size_t off_tb = off_lp + sizeof(int) * NV;  // tile mesh bytes
-  static constexpr size_t bytes = off_tb + ((NV + 15) / 16) * 16;
+  static constexpr size_t off_rows = off_tb + ((NV + 15) / 16) * 16;  // long long [HR] input row offsets
+  static constexpr size_t bytes = off_rows + sizeof(long long) * HR;
   static constexpr size_t ccl_bytes = sizeof(int) * NV + ((NV + 15) / 16) * 16;
 };
 
-// Issue the asynchronous copy of scan row i at the lane's column into its
-// ring slot (x,y,z,r input), or store the decoded / absent value directly.
+// Issue the asynchronous copy of one point into the lane's ring slot (x,y,z,r
+// input), or store the decoded / absent value directly.  ro = offset of the
+// input row (ring order * W), or -1 when the row is outside the scan.
 __device__ __forceinline__ void fetch_point(float4* slot, const float4* __restrict__ xyzr,
-                                            const float* __restrict__ range, const int32_t* __restrict__ order,
-                                            const float2* __restrict__ trig, int H, int W, int i, bool colok,
-                                            size_t coff, float sp, float cp) {
-  if (colok && i >= 0 && i < H) {
-    const int row = __ldg(order + i);
-    if ((unsigned)row < (unsigned)H) {
-      const size_t o = (size_t)row * W + coff;
-      if (xyzr) {
-        const unsigned dst = (unsigned)__cvta_generic_to_shared(slot);
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(xyzr + o) : "memory");
-      } else {
-        const float r = __ldg(range + o);
-        const float2 te = __ldg(trig + i);
-        const float rc = r * te.y;
-        *slot = make_float4(rc * cp, rc * sp, r * te.x, r);
-      }
-      return;
+                                            const float* __restrict__ range, const float2* __restrict__ trig,
+                                            int i, long long ro, bool colok, size_t coff, float sp, float cp) {
+  if (colok && ro >= 0) {
+    const size_t o = (size_t)ro + coff;
+    if (xyzr) {
+      const unsigned dst = (unsigned)__cvta_generic_to_shared(slot);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(xyzr + o) : "memory");
+    } else {
+      const float r = __ldg(range + o);
+      const float2 te = __ldg(trig + i);
+      const float rc = r * te.y;
+      *slot = make_float4(rc * cp, rc * sp, r * te.x, r);
     }
+    return;
   }
   *slot = make_float4(0.f, 0.f, 0.f, -1.f);
 }
@@ -404,6 +404,18 @@ __device__ __forceinline__ void tile_body(const ScanDesc* d, int lt, unsigned ch
   const int32_t* __restrict__ order = d->order;
   const float2* __restrict__ trig = d->trig;
   const float rmin = d->r_min, rmax = d->r_max, jh = d->jump_h, jv = d->jump_v;
+  // offsets of the input rows the tile reads (ring order applied once)
+  long long* rows_s = reinterpret_cast<long long*>(smem + G::off_rows);
+  for (int k = threadIdx.x; k < L.rn + 3; k += G::NT) {
+    const int i = L.r0 - 1 + k;
+    long long ro = -1;
+    if (i >= 0 && i < L.H) {
+      const int row = __ldg(order + i);
+      if ((unsigned)row < (unsigned)L.H) ro = (long long)row * L.W;
+    }
+    rows_s[k] = ro;
+  }
+  __syncthreads();
 
   // The sweep: warp w owns tile columns w*29-1 .. w*29+30 (one per lane),
   // of which lanes 1..29 are its output columns.  Each lane streams its
@@ -442,9 +454,10 @@ __device__ __forceinline__ void tile_body(const ScanDesc* d, int lt, unsigned ch
     float4 n_pp = make_float4(0.f, 0.f, 0.f, 0.f);             // normal of row k-2
     const int rbase = L.r0 - 1;
     const int nsteps = L.rn + 3;
+    size_t vout = (size_t)L.r0 * L.Ws + (size_t)(L.c0 + lc);  // output vertex of tile row 0
 #pragma unroll
     for (int q = 0; q < RING; ++q) {
-      if (q < nsteps) fetch_point(ring + q * 32, xyzr, range, order, trig, L.H, L.W, rbase + q, colok, coff, sp, cp);
+      if (q < nsteps) fetch_point(ring + q * 32, xyzr, range, trig, rbase + q, rows_s[q], colok, coff, sp, cp);
       asm volatile("cp.async.commit_group;\n" ::: "memory");
     }
 
@@ -454,8 +467,8 @@ __device__ __forceinline__ void tile_body(const ScanDesc* d, int lt, unsigned ch
       float4 P = ring[(hr % (RING + 1)) * 32];
       // refill: the slot of row hr+RING was last read one step ago
       if (hr + RING < nsteps)
-        fetch_point(ring + ((hr + RING) % (RING + 1)) * 32, xyzr, range, order, trig, L.H, L.W, rbase + hr + RING,
-                    colok, coff, sp, cp);
+        fetch_point(ring + ((hr + RING) % (RING + 1)) * 32, xyzr, range, trig, rbase + hr + RING,
+                    rows_s[hr + RING], colok, coff, sp, cp);
       asm volatile("cp.async.commit_group;\n" ::: "memory");
       if (!in_range(P.w, rmin, rmax)) P = make_float4(0.f, 0.f, 0.f, P.w);  // finite spokes only
       float4 Pr;
@@ -520,19 +533,19 @@ __device__ __forceinline__ void tile_body(const ScanDesc* d, int lt, unsigned ch
         const float4 nr_p = make_float4(__shfl_down_sync(FULL, n_p.x, 1), __shfl_down_sync(FULL, n_p.y, 1),
                                         __shfl_down_sync(FULL, n_p.z, 1), __shfl_down_sync(FULL, n_p.w, 1));
         const int lr = hr - 3;
+        uint32_t bits = m_pp | (n_pp.w != 0.f ? B_HASN : 0u);
+        bits |= ((m_pp & B_R) && homog(n_pp, nr_pp, angle_pred, cos_t, cx, cy, cz)) ? B_HR : 0u;
+        bits |= ((m_pp & B_D) && homog(n_pp, n_p, angle_pred, cos_t, cx, cy, cz)) ? B_HD : 0u;
+        bits |= ((m_pp & B_G) && homog(n_pp, nr_p, angle_pred, cos_t, cx, cy, cz)) ? B_HG : 0u;
         if (out_col && lr < L.rn) {
-          uint32_t bits = m_pp;
-          if (n_pp.w != 0.f) bits |= B_HASN;
-          if ((m_pp & B_R) && homog(n_pp, nr_pp, angle_pred, cos_t, cx, cy, cz)) bits |= B_HR;
-          if ((m_pp & B_D) && homog(n_pp, n_p, angle_pred, cos_t, cx, cy, cz)) bits |= B_HD;
-          if ((m_pp & B_G) && homog(n_pp, nr_p, angle_pred, cos_t, cx, cy, cz)) bits |= B_HG;
-          const size_t v = (size_t)(L.r0 + lr) * L.Ws + (L.c0 + lc);
+          const size_t v = vout;
           mb_out[v] = (uint8_t)bits;
           nrm_out[3 * v + 0] = n_pp.x;
           nrm_out[3 * v + 1] = n_pp.y;
           nrm_out[3 * v + 2] = n_pp.z;
           tb[lr * TC + lc] = (uint8_t)bits;
         }
+        vout += L.Ws;
       }
 
       // rotate the window
@@ -563,7 +576,7 @@ __device__ __forceinline__ void tile_body(const ScanDesc* d, int lt, unsigned ch
 }
 
 template <int TR, int NW>
-__global__ void __launch_bounds__(NW * 32) k_tile(const __grid_constant__ KArgs a) {
+__global__ void __launch_bounds__(NW * 32, 24 / NW) k_tile(const __grid_constant__ KArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
     int lt;
