@@ -297,6 +297,26 @@ lsg_status lsg_plan_destroy(lsg_plan* plan);
  * device).  LSG_OK when no device-side error was recorded. */
 lsg_status lsg_get_error(lsg_ctx* ctx);
 
+/*
+ * Per-segment statistics and small-segment removal: the optional
+ * post-processing of Sec. 2 (last paragraph), which eliminates segments with
+ * too few points.  Runs on the outputs of lsg_segment, in place.
+ *   H, W, s       grid of the scan (as in lsg_segment)
+ *   min_points    segments of fewer points become -1 (0 keeps every segment)
+ *   labels        device int32[H][W], in/out
+ *   sizes         device int32[H*W], out: sizes[L] = number of points whose
+ *                 label was L before removal (0 where L is not a label)
+ *   nsum          device float[H*W][3], out, or NULL: nsum[L] = sum of the
+ *                 unit normals of the segment's vertices that have one (its
+ *                 direction is the segment's mean normal); float atomics, so
+ *                 the summation order (last bits) varies from run to run
+ *   normals, meshbits  lsg_segment's outputs (read only when nsum != NULL)
+ *   nseg          device int32[1], out: number of segments kept
+ */
+lsg_status lsg_segment_stats(lsg_ctx* ctx, int32_t H, int32_t W, int32_t s, int32_t min_points,
+                             int32_t* labels, const float* normals, const uint8_t* meshbits, int32_t* sizes,
+                             float* nsum, int32_t* nseg, lsg_stream stream);
+
 /* Largest scan (rings x sampled columns) lsg_segment_noalloc accepts. */
 #define LSG_NOALLOC_MAX_VERTICES (1 << 20)
 

@@ -540,3 +540,42 @@ int oracle_label_from_mask(int H, int W, int s, int wrap, const unsigned char* m
   free(vlabel);
   return n < 0 ? -2 : 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Post-processing: segment sizes and small-segment removal                  */
+/* (Sec. 2, last paragraph: segments with too few points may be eliminated)  */
+/* ------------------------------------------------------------------------ */
+
+/* labels_in[H*W]: labels as produced by the path (-1 or the segment's
+ * smallest point index).  sizes[H*W]: number of points carrying each label
+ * (0 for indices that are not labels).  nsum[3*H*W] (optional): sum of the
+ * unit normals of the segment's mesh vertices that have one (vertex (i, j)
+ * carries labels_in[i*W + j*s]).  labels_out: labels_in with every segment of
+ * fewer than min_points points set to -1.  Returns the number of segments
+ * kept. */
+int oracle_segment_stats(int H, int W, int s, const int32_t* labels_in, const double* normal,
+                         const unsigned char* mb, int min_points, int32_t* labels_out, int32_t* sizes,
+                         double* nsum) {
+  size_t N = (size_t)H * W;
+  int Ws = (W + s - 1) / s;
+  for (size_t p = 0; p < N; ++p) sizes[p] = 0;
+  if (nsum)
+    for (size_t p = 0; p < 3 * N; ++p) nsum[p] = 0.0;
+  for (size_t p = 0; p < N; ++p)
+    if (labels_in[p] >= 0) sizes[labels_in[p]] += 1;
+  if (nsum && normal && mb)
+    for (int i = 0; i < H; ++i)
+      for (int j = 0; j < Ws; ++j) {
+        size_t v = (size_t)i * Ws + j;
+        int32_t lab = labels_in[(size_t)i * W + (size_t)j * s];
+        if (lab < 0 || !(mb[v] & OB_HASN)) continue;
+        for (int t = 0; t < 3; ++t) nsum[3 * (size_t)lab + t] += normal[3 * v + t];
+      }
+  int kept = 0;
+  for (size_t p = 0; p < N; ++p) {
+    int32_t lab = labels_in[p];
+    labels_out[p] = (lab >= 0 && sizes[lab] >= min_points) ? lab : -1;
+    if (lab >= 0 && (size_t)lab == p && sizes[lab] >= min_points) ++kept;
+  }
+  return kept;
+}

@@ -64,6 +64,7 @@ def _load():
             "oracle_segment": [I, I, _P, F, F, _P, _P, I, F, F, F, F, I, D, _P, I, _P, _P, _P, _P, _P,
                                _P, _P, _P, _P, _P],
             "oracle_label_from_mask": [I, I, I, I, _P, _P, _P, _P],
+            "oracle_segment_stats": [I, I, I, _P, _P, _P, I, _P, _P, _P],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -270,6 +271,23 @@ def label_from_mask(mb, valid, W, s, wrap):
     return labels, int(nseg[0])
 
 
+def segment_stats(labels, min_points, W=None, s=1, normals=None, meshbits=None):
+    """Sizes of the segments, optional normal sums, and labels with the
+    segments of fewer than min_points points removed (Sec. 2, last
+    paragraph).  Returns (labels_out, sizes, nsum or None, kept)."""
+    lib = _load()
+    labels = _c(labels, np.int32)
+    H, W_ = labels.shape
+    out = np.empty_like(labels)
+    sizes = np.zeros(H * W_, np.int32)
+    nsum = np.zeros((H * W_, 3), np.float64) if normals is not None else None
+    nrm = _c(normals, np.float64) if normals is not None else None
+    mb = _c(meshbits, np.uint8) if meshbits is not None else None
+    kept = lib.oracle_segment_stats(H, W_, int(s), _ptr(labels), _ptr(nrm), _ptr(mb), int(min_points), _ptr(out),
+                                    _ptr(sizes), _ptr(nsum))
+    return out, sizes, nsum, kept
+
+
 def angle(a, b) -> float:
     a = _c(a, np.float64)
     b = _c(b, np.float64)
@@ -278,5 +296,6 @@ def angle(a, b) -> float:
 
 __all__ = ["Params", "Result", "segment", "segment_scan", "ring_order", "decode", "mesh", "neighbours",
            "normals", "edge_mask", "components", "algorithm1", "backfill", "label_from_mask", "angle",
+           "segment_stats",
            "ws_of", "build", "PRED_ANGLE", "PRED_COMPONENT", "BIT_R", "BIT_D", "BIT_G", "BIT_HR",
            "BIT_HD", "BIT_HG", "BIT_VALID", "BIT_HASN"]

@@ -91,6 +91,7 @@ def load(build: bool = True):
             "lsg_plan_phase_times": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float)]),
             "lsg_plan_destroy": (ctypes.c_int, [_P]),
             "lsg_get_error": (ctypes.c_int, [_P]),
+            "lsg_segment_stats": (ctypes.c_int, [_P, I32, I32, I32, I32, _P, _P, _P, _P, _P, _P, _P]),
             "lsg_segment_noalloc": (ctypes.c_int, [ctypes.POINTER(lsg_scan), ctypes.POINTER(lsg_params),
                                                    ctypes.POINTER(lsg_out), _P]),
             "lsg_default_params": (None, [ctypes.POINTER(lsg_params)]),
@@ -349,6 +350,23 @@ class Context:
                                  _stream_ptr(stream))
         _check(st, "lsg_label_from_mask")
         return labels, nseg
+
+    def segment_stats(self, out: Outputs, W: int, s: int, min_points: int, normal_sums: bool = False, stream=None):
+        """Sizes of out's segments (indexed by label), optional normal sums, and
+        removal (in place) of segments of fewer than min_points points."""
+        import torch
+        H = int(out.labels.shape[0])
+        dev = out.labels.device
+        sizes = torch.empty(max(H * W, 1), dtype=torch.int32, device=dev)
+        nsum = torch.empty((max(H * W, 1), 3), dtype=torch.float32, device=dev) if normal_sums else None
+        nseg = torch.zeros(1, dtype=torch.int32, device=dev)
+        st = load().lsg_segment_stats(self.h, H, W, s, min_points, out.labels.data_ptr() if out.labels.numel() else None,
+                                      out.normals.data_ptr() if out.normals.numel() else None,
+                                      out.meshbits.data_ptr() if out.meshbits.numel() else None, sizes.data_ptr(),
+                                      nsum.data_ptr() if nsum is not None else None, nseg.data_ptr(),
+                                      _stream_ptr(stream))
+        _check(st, "lsg_segment_stats")
+        return sizes, nsum, nseg
 
     def error(self) -> int:
         return lsg_get_error(self.h)

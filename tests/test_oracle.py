@@ -514,3 +514,35 @@ def test_empty_and_degenerate_shapes():
     xyzr = np.zeros((3, 5, 4), np.float32)
     r = O.segment(np.zeros(3, np.float32), 0.0, 0.01, xyzr, p)
     assert r.nseg == 0 and (r.labels == -1).all()
+
+
+# --------------------------------------------------------------------------
+# post-processing: segment sizes and small-segment removal (Sec. 2, last paragraph)
+# --------------------------------------------------------------------------
+def test_segment_stats_hand_worked():
+    # two rings of 6 points; labels are smallest point indices of their segments
+    lab = np.array([[0, 0, 0, -1, 4, 4],
+                    [0, 7, 7, 7, 7, -1]], np.int32)
+    out, sizes, _, kept = O.segment_stats(lab, 3)
+    assert sizes[0] == 4 and sizes[4] == 2 and sizes[7] == 4 and sizes.sum() == 10
+    assert kept == 2
+    assert out.tolist() == [[0, 0, 0, -1, -1, -1], [0, 7, 7, 7, 7, -1]]
+    out1, _, _, kept1 = O.segment_stats(lab, 1)
+    assert kept1 == 3 and np.array_equal(out1, lab)
+
+
+def test_segment_stats_on_a_scan_are_consistent():
+    spec = lidarsim.ring16()
+    scan = lidarsim.make_scan(spec)
+    r = O.segment_scan(scan, params_for(spec))
+    out, sizes, nsum, kept = O.segment_stats(r.labels, 5, normals=r.normals, meshbits=r.meshbits)
+    labelled = r.labels >= 0
+    assert sizes.sum() == labelled.sum()
+    # every removed point belonged to a segment of fewer than 5 points
+    removed = labelled & (out < 0)
+    assert np.all(sizes[r.labels[removed]] < 5)
+    assert kept == int(np.sum(sizes >= 5))
+    # a normal sum is never longer than the number of vertices summed
+    lens = np.linalg.norm(nsum, axis=1)
+    assert np.all(lens <= sizes + 1e-9)
+    assert kept <= r.nseg
