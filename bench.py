@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--phased", action="store_true", help="force four phased launches (else the autotuner's choice)")
     ap.add_argument("--fused", action="store_true", help="force the single persistent launch")
-    ap.add_argument("--tile", default=None, help="force a tile shape (e.g. 32x116) instead of autotuning")
+    ap.add_argument("--tile", default=None, help="force a tile shape (e.g. 32x240) instead of autotuning")
     ap.add_argument("--serve-scale", type=float, default=10.0,
                     help="time compression of the 60 s sensor trace for the served measurement")
     return ap.parse_args()

@@ -152,15 +152,16 @@ typedef struct {
 } lsg_out;
 
 /* Tile shapes of the fused kernels: rows x columns of mesh vertices per CTA.
- * Each warp of a CTA sweeps a strip of 29 columns down the tile's rows, so
- * the widths are multiples of 29 (4 warps: 116, 8 warps: 232). */
+ * Each warp of a CTA sweeps a strip of 60 columns (two per lane) down the
+ * tile's rows, so the widths are multiples of 60 (2 warps: 120, 4 warps:
+ * 240, 8 warps: 480). */
 enum {
   LSG_TILE_AUTO = -1,
-  LSG_TILE_16x116 = 0,
-  LSG_TILE_32x116 = 1,
-  LSG_TILE_32x232 = 2,
-  LSG_TILE_64x116 = 3,
-  LSG_TILE_64x232 = 4,
+  LSG_TILE_16x240 = 0,
+  LSG_TILE_32x120 = 1,
+  LSG_TILE_32x240 = 2,
+  LSG_TILE_32x480 = 3,
+  LSG_TILE_64x240 = 4,
   LSG_TILE_COUNT = 5
 };
 

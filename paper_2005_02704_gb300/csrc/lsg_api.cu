@@ -31,14 +31,14 @@ struct lsg_ctx {
   void* ws = nullptr;       // single-scan / dynamic-batch workspace
   size_t ws_bytes = 0;
   int32_t* d_err = nullptr; // sticky device error word
-  int tile = LSG_TILE_16x116;
+  int tile = LSG_TILE_32x240;
   DynStage stage[2];        // alternated by successive lsg_batch_launch calls
   int next_stage = 0;
 };
 
 struct lsg_plan {
   lsg_ctx* ctx = nullptr;
-  int tile = LSG_TILE_16x116;
+  int tile = LSG_TILE_32x240;
   int n = 0;
   std::vector<ScanDesc> host_desc;  // tile fields filled per tile shape
   ScanDesc* d_desc = nullptr;
@@ -278,7 +278,7 @@ lsg_status lsg_destroy(lsg_ctx* ctx) {
 
 lsg_status lsg_set_tile(lsg_ctx* ctx, int tile) {
   if (!ctx) return LSG_E_ARG;
-  if (tile == LSG_TILE_AUTO) tile = LSG_TILE_16x116;
+  if (tile == LSG_TILE_AUTO) tile = LSG_TILE_32x240;
   if (tile < 0 || tile >= LSG_TILE_COUNT) return LSG_E_ARG;
   ctx->tile = tile;
   return LSG_OK;
@@ -637,10 +637,10 @@ lsg_status lsg_batch_plan(lsg_ctx* ctx, int32_t n, const lsg_scan* scans, const 
     if (st != LSG_OK) return st;
     ws_total += scan_ws_bytes(scans[b].rings, Ws[b]);
   }
-  // bound on the tile table over every tile shape (at least 16 rows x 116 columns)
+  // bound on the tile table over every tile shape (at least 16 rows x 120 columns)
   size_t tiles_max = 0;
   for (int b = 0; b < n; ++b)
-    tiles_max += (size_t)(scans[b].rings / 16 + 1) * (Ws[b] / 116 + 1);
+    tiles_max += (size_t)(scans[b].rings / 16 + 1) * (Ws[b] / 120 + 1);
   // workspace, descriptors, tile table, fused schedule (scan + 3 items per tile) and counters
   const size_t bytes = ws_total + align_up(sizeof(ScanDesc) * n, 256) + sizeof(int32_t) * tiles_max +
                        sizeof(int2) * (n + 3 * tiles_max) + sizeof(int32_t) * (1 + 3 * (size_t)n);

@@ -6,20 +6,23 @@
 //
 //   k_prep     ring order by elevation (rank counting), sin/cos of the sorted
 //              elevations, segment counter reset.               [Sec. 2, point model]
-//   k_tile     one CTA per tile of TR rows x (29*NW) columns of mesh vertices.
-//              The CTA stages x,y,z,r of the tile plus a halo (one ring above,
-//              two below, one column left, two right) in shared memory.  Each
-//              warp then sweeps a strip of 32 columns (29 of them its own)
-//              down the rows, holding a three-row window in registers and
-//              taking the neighbouring columns from the adjacent lanes with
-//              warp shuffles: mesh bits and edge vectors of each row, the
-//              weighted normal of the row above, the homogeneity mask of the
-//              row above that.  Every edge vector and length is computed once
-//              and reused by both endpoints.  The tile's components follow:
-//              horizontal runs from a warp ballot, vertical joins with an
-//              atomicMin union-find in shared memory (only where a run meets a
-//              new run above), then joins across strips.  Writes the mesh byte,
-//              the normal, and each vertex's tile-local root (16 bits).
+//   k_tile     one CTA per tile of TR rows x (60*NW) columns of mesh vertices.
+//              Each warp sweeps a strip of 64 columns (60 of them its own, two
+//              per lane) down the rows: every lane streams its two columns'
+//              x,y,z,r rows into shared-memory ring slots with cp.async a few
+//              rows ahead, holds a three-row window in registers, and takes
+//              the neighbouring columns from the adjacent lanes with warp
+//              shuffles.  The geometry runs on packed binary32 pairs (both
+//              columns in one instruction): mesh bits and edge vectors of
+//              each row, the weighted normal of the row above, the
+//              homogeneity mask of the row above that.  Every edge vector and
+//              length is computed once and reused by both endpoints.  The
+//              tile's components follow: horizontal runs from two warp
+//              ballots, vertical joins with an atomicMin union-find over the
+//              runs' first vertices in shared memory (only where the column to
+//              the left does not already join the same two vertices), then
+//              joins across strips.  Writes the mesh byte, the normal, and each
+//              vertex's tile-local root (16 bits).
 //                                          [Sec. 2 mesh, normals; Algorithm 1]
 //   k_merge    joins tile-local components across tile borders and the 360 deg
 //              seam with a lock-free atomicMin union-find over the roots.
@@ -31,6 +34,7 @@
 // each component's root is its smallest vertex index whatever the thread
 // order, and a tile-local root is the smallest index of its tile component.
 #include <cuda_runtime.h>
+#include <float.h>
 #include <limits.h>
 #include <stdint.h>
 
@@ -42,7 +46,7 @@ constexpr uint8_t B_R = LSG_BIT_R, B_D = LSG_BIT_D, B_G = LSG_BIT_G;
 constexpr uint8_t B_HR = LSG_BIT_HR, B_HD = LSG_BIT_HD, B_HG = LSG_BIT_HG;
 constexpr uint8_t B_VALID = LSG_BIT_VALID, B_HASN = LSG_BIT_HASN;
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int SO = 29;  // output columns per warp strip (lanes 1..29)
+constexpr int SO = 60;  // output columns per warp strip (lanes 1..30, two columns each)
 constexpr uint16_t NO_ROOT = 0xFFFF;  // tile-local root of a vertex out of range
 
 // Row pitch of the tile-root array: Ws rounded up to 8 entries (16 bytes), so
@@ -51,12 +55,12 @@ __host__ __device__ __forceinline__ int root_pitch(int Ws) { return (Ws + 7) & ~
 
 TileShape tile_shape(int tile) {
   switch (tile) {
-    case LSG_TILE_32x116: return {32, 116};
-    case LSG_TILE_32x232: return {32, 232};
-    case LSG_TILE_64x116: return {64, 116};
-    case LSG_TILE_64x232: return {64, 232};
-    case LSG_TILE_16x116:
-    default: return {16, 116};
+    case LSG_TILE_32x120: return {32, 120};
+    case LSG_TILE_32x240: return {32, 240};
+    case LSG_TILE_32x480: return {32, 480};
+    case LSG_TILE_64x240: return {64, 240};
+    case LSG_TILE_16x240:
+    default: return {16, 240};
   }
 }
 
@@ -65,42 +69,6 @@ TileShape tile_shape(int tile) {
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ bool in_range(float r, float rmin, float rmax) {
   return rmin < r && r <= rmax;
-}
-
-// Depth-jump cut |r_p - r_q| > tau * min(r_p, r_q) in binary32, round to
-// nearest, never contracted into an FMA (the decision must be reproducible).
-__device__ __forceinline__ bool jump_cut(float rp, float rq, float tau) {
-  const float d = fabsf(__fsub_rn(rp, rq));
-  return d > __fmul_rn(tau, fminf(rp, rq));
-}
-
-// Length of a vector via the hardware reciprocal square root (about 2 ulp).
-__device__ __forceinline__ float vlen(float x, float y, float z) {
-  const float q = fmaf(x, x, fmaf(y, y, z * z));
-  return q > 0.f ? q * rsqrtf(q) : 0.f;
-}
-
-// One weighted triangle term of the normal sum (Sec. 2, normal estimation):
-// w (a x b) with w = 1 / (|a| + |b|), added only when the triangle exists.
-// The sweep zeroes the coordinates of points out of range, so every spoke is
-// finite and a missing triangle's term is removed by a zero weight.
-__device__ __forceinline__ void tri_term(float ax, float ay, float az, float la, float bx, float by, float bz,
-                                         float lb, bool exists, float& sx, float& sy, float& sz) {
-  const float w = exists ? __fdividef(1.0f, la + lb) : 0.f;  // hardware reciprocal, <= 2 ulp
-  sx = fmaf(w, ay * bz - az * by, sx);
-  sy = fmaf(w, az * bx - ax * bz, sy);
-  sz = fmaf(w, ax * by - ay * bx, sz);
-}
-
-// Homogeneity predicate of Algorithm 1 between two vertices' normals
-// (w = 1 when the vertex has a normal).
-// Branch-free: both forms are evaluated and the predicate selects one.
-__device__ __forceinline__ bool homog(const float4 u, const float4 v, bool angle_pred, float cos_t, float cx,
-                                      float cy, float cz) {
-  const bool both = (u.w != 0.f) & (v.w != 0.f);
-  const bool by_angle = fmaf(u.x, v.x, fmaf(u.y, v.y, u.z * v.z)) > cos_t;
-  const bool by_comp = (fabsf(u.x - v.x) < cx) & (fabsf(u.y - v.y) < cy) & (fabsf(u.z - v.z) < cz);
-  return both & (angle_pred ? by_angle : by_comp);
 }
 
 __device__ __forceinline__ const ScanDesc* tile_desc(const KArgs& a, int t, int& lt) {
@@ -115,20 +83,25 @@ __device__ __forceinline__ const ScanDesc* tile_desc(const KArgs& a, int t, int&
 
 // Union-find on shared memory.  P[x] <= x always holds, so the forest has no
 // cycles and the root of every tree is its smallest index.
-__device__ __forceinline__ int find_s(volatile int* P, int x, int limit) {
-  int p = P[x];
+// find with path halving on shared memory: each visited node is re-pointed
+// at its grandparent.  The store only shortens a path to an ancestor
+// (P[x] <= x still holds), so it is safe next to concurrent atomicMin links.
+__device__ __forceinline__ int find_sh(int* P, int x, int limit) {
+  volatile int* V = P;
+  int p = V[x];
   while (p != x && limit-- > 0) {
-    x = p;
-    p = P[x];
+    const int gp = V[p];
+    if (gp != p) V[x] = gp;
+    x = gp;
+    p = V[x];
   }
   return x;
 }
 
-__device__ void union_s(int* P, int a, int b, int limit, int32_t* err) {
-  volatile int* V = P;
+__device__ void union_sh(int* P, int a, int b, int limit, int32_t* err) {
   for (int it = 0; it < limit; ++it) {
-    a = find_s(V, a, limit);
-    b = find_s(V, b, limit);
+    a = find_sh(P, a, limit);
+    b = find_sh(P, b, limit);
     if (a == b) return;
     if (a > b) {
       const int t = a;
@@ -225,7 +198,8 @@ __global__ void __launch_bounds__(NT_PREP) k_prep(const __grid_constant__ KArgs 
 // ---------------------------------------------------------------------------
 // tile geometry
 // ---------------------------------------------------------------------------
-constexpr int RING = 8;  // rows each lane keeps in flight (cp.async depth)
+constexpr int RING = 4;  // row slots per lane and point (RING - 1 rows in flight)
+constexpr int QCAP = 256;  // pending tile unions per warp (flushed before it can overflow)
 
 template <int TR, int NW>
 struct Geo {
@@ -233,20 +207,33 @@ struct Geo {
   static constexpr int TC = NW * SO;             // output columns of a tile
   static constexpr int HR = TR + 3;              // rows read: r0-1 .. r0+TR+1
   static constexpr int NV = TR * TC;
-  static constexpr size_t off_ring = 0;          // per-warp row rings [NW][RING+1][32] float4
-  static constexpr size_t off_lp = off_ring + sizeof(float4) * NW * (RING + 1) * 32;  // tile union-find
-  static constexpr size_t off_tb = off_lp + sizeof(int) * NV;  // tile mesh bytes
+  // The sweep's per-warp row rings [NW][RING][2][32] float4 and, once the
+  // sweep is over, the tile union-find int[NV] share the first region.
+  static constexpr size_t ring_bytes = sizeof(float4) * NW * RING * 64;
+  static constexpr size_t lp_bytes = sizeof(int) * NV;
+  static constexpr size_t off_ring = 0;
+  static constexpr size_t off_lp = 0;
+  static constexpr size_t off_tb = ((ring_bytes > lp_bytes ? ring_bytes : lp_bytes) + 15) / 16 * 16;
   static constexpr size_t off_rows = off_tb + ((NV + 15) / 16) * 16;  // long long [HR] input row offsets
-  static constexpr size_t bytes = off_rows + sizeof(long long) * HR;
-  static constexpr size_t ccl_bytes = sizeof(int) * NV + ((NV + 15) / 16) * 16;
+  static constexpr size_t off_q = off_rows + ((sizeof(long long) * HR + 15) / 16) * 16;  // uint32 [NW][QCAP]
+  static constexpr size_t q_bytes = sizeof(uint32_t) * NW * QCAP;
+  static constexpr size_t bytes = off_q + q_bytes;
+  static constexpr size_t ccl_bytes = lp_bytes + ((NV + 15) / 16) * 16 + q_bytes;  // k_tile_ccl: lp, tb, queue
 };
 
-// Issue the asynchronous copy of one point into the lane's ring slot (x,y,z,r
-// input), or store the decoded / absent value directly.  ro = offset of the
-// input row (ring order * W), or -1 when the row is outside the scan.
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Issue the asynchronous copy of one point into a ring slot (x,y,z,r input),
+// or store the decoded / absent value directly.  ro = offset of the input
+// row (ring order * W), or -1 when the row is outside the scan.
 __device__ __forceinline__ void fetch_point(float4* slot, const float4* __restrict__ xyzr,
                                             const float* __restrict__ range, const float2* __restrict__ trig,
-                                            int i, long long ro, bool colok, size_t coff, float sp, float cp) {
+                                            int i, long long ro, bool colok, unsigned coff, float sp, float cp) {
   if (colok && ro >= 0) {
     const size_t o = (size_t)ro + coff;
     if (xyzr) {
@@ -285,62 +272,443 @@ __device__ __forceinline__ Loc make_loc(const ScanDesc* d, int lt, int TR, int T
   return L;
 }
 
+// Sampled column j taken around the ring (wrap only: Ws >= 3).
+__device__ __forceinline__ int wrap_col(int j, int Ws) {
+  if (j < 0) j += Ws;
+  else if (j >= Ws) j -= Ws;
+  if (j < 0 || j >= Ws) j = ((j % Ws) + Ws) % Ws;
+  return j;
+}
+
+// ---------------------------------------------------------------------------
+// packed binary32 arithmetic: a lane's two columns in one instruction
+// (.x: the lane's first column, .y: its second)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// a - b rounded once (b * -1 is exact), as a binary32 subtraction
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+// Hardware approximations (PTX rsqrt.approx / rcp.approx, flush-to-zero):
+// relative error below 2^-22 and 1 ulp respectively.
+__device__ __forceinline__ float rsq_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Lengths of two vectors: q * rsqrt(q), exact 0 for a zero vector.
+__device__ __forceinline__ float2 len2(float2 x, float2 y, float2 z) {
+  const float2 q = fma2(x, x, fma2(y, y, mul2(z, z)));
+  return mul2(q, make_float2(rsq_approx(fmaxf(q.x, FLT_MIN)), rsq_approx(fmaxf(q.y, FLT_MIN))));
+}
+
+// Depth-jump cut of two edges: |r_p - r_q| > tau * min(r_p, r_q) in
+// binary32, round to nearest, never contracted (reproducible decisions).
+__device__ __forceinline__ void jump_cut2(float2 rp, float2 rq, float2 tau, bool& ca, bool& cb) {
+  const float2 dd = sub2(rp, rq);
+  const float2 t = mul2(tau, make_float2(fminf(rp.x, rq.x), fminf(rp.y, rq.y)));
+  ca = fabsf(dd.x) > t.x;
+  cb = fabsf(dd.y) > t.y;
+}
+
+// One weighted triangle term of two vertices' normal sums (Sec. 2, normal
+// estimation): w (a x b) with w = 1 / (|a| + |b|), added only where the
+// triangle exists.  Points out of range have zero coordinates, so every
+// spoke is finite and a missing triangle's term is removed by a zero weight.
+__device__ __forceinline__ void tri2(float2 ax, float2 ay, float2 az, float2 la, float2 bx, float2 by, float2 bz,
+                                     float2 lb, bool ta, bool tb, float2& sx, float2& sy, float2& sz) {
+  const float2 l = add2(la, lb);
+  const float2 wt = make_float2(ta ? rcp_approx(l.x) : 0.f, tb ? rcp_approx(l.y) : 0.f);
+  const float2 cx = fma2(ay, bz, mul2(neg2(az), by));
+  const float2 cy = fma2(az, bx, mul2(neg2(ax), bz));
+  const float2 cz = fma2(ax, by, mul2(neg2(ay), bx));
+  sx = fma2(wt, cx, sx);
+  sy = fma2(wt, cy, sy);
+  sz = fma2(wt, cz, sz);
+}
+
+// Homogeneity predicate of Algorithm 1 for two vertex pairs.  A vertex
+// without a normal carries NaN components, which fail either comparison.
+template <bool ANGLE>
+__device__ __forceinline__ void homog2(float2 ux, float2 uy, float2 uz, float2 vx, float2 vy, float2 vz, float cos_t,
+                                       float cx, float cy, float cz, bool& ha, bool& hb) {
+  if (ANGLE) {
+    const float2 dt = fma2(ux, vx, fma2(uy, vy, mul2(uz, vz)));
+    ha = dt.x > cos_t;
+    hb = dt.y > cos_t;
+  } else {
+    const float2 ex = sub2(ux, vx), ey = sub2(uy, vy), ez = sub2(uz, vz);
+    ha = (fabsf(ex.x) < cx) & (fabsf(ey.x) < cy) & (fabsf(ez.x) < cz);
+    hb = (fabsf(ex.y) < cx) & (fabsf(ey.y) < cy) & (fabsf(ez.y) < cz);
+  }
+}
+
+__device__ __forceinline__ float2 left_of(float2 v) {
+  return make_float2(__shfl_up_sync(FULL, v.y, 1), v.x);
+}
+__device__ __forceinline__ float2 right_of(float2 v) {
+  return make_float2(v.y, __shfl_down_sync(FULL, v.x, 1));
+}
+
+// ---------------------------------------------------------------------------
+// k_tile: decode + mesh + normals + edge mask + tile components
+// ---------------------------------------------------------------------------
+// The sweep of one tile.  Warp w owns tile columns w*60-2 .. w*60+61, two
+// per lane (lane l: columns w*60+2l-2 and w*60+2l-1); lanes 1..30 hold its
+// 60 output columns, lanes 0 and 31 the halo.  Each lane streams its two
+// columns' rows into its own shared-memory ring slots with cp.async, RING-1
+// rows ahead of use (coalesced 16-byte copies; a lane reads only slots it
+// filled, so no barrier).  At step hr it holds scan row k = r0-1+hr and
+// completes: the R edges of row k and the D and G edges of row k-1; the
+// normals of row k-1 (Sec. 2, normal estimation), whose three terms
+// through row k-2 were summed one step earlier; the three terms of row k's
+// normals through row k-1; and the homogeneity mask and outputs of row k-2
+// (Algorithm 1 predicate).
+//
+// Spokes of a vertex p in the paper's order: A (down), B (down-right),
+// C (right), D (up), E (up-left), F (left).  With d, g, r the D, G and R
+// edge vectors leaving a vertex and gl, f the G and R edges arriving at it,
+// the six terms are  A x B = d x g,  B x C = g x r,  F x A = d x f  (below p)
+// and  C x D = d' x r,  D x E = d' x gl',  E x F = gl' x f  (above p, with
+// d', gl' the edges from the row above): reversed spokes are folded into the
+// operand order.  A triangle (p, q, q') counts when its three edges exist.
+template <int TR, int NW, bool ANGLE, bool XYZR>
+__device__ __forceinline__ void tile_sweep(const ScanDesc* d, const Loc& L, unsigned char* smem) {
+  using G = Geo<TR, NW>;
+  constexpr int TC = G::TC;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  float4* ring = reinterpret_cast<float4*>(smem + G::off_ring) + (size_t)w * (RING * 64) + lane;
+  const long long* rows_s = reinterpret_cast<const long long*>(smem + G::off_rows);
+  uint8_t* tb = smem + G::off_tb;
+  const float4* __restrict__ xyzr = d->xyzr;
+  const float* __restrict__ range = d->range;
+  const float2* __restrict__ trig = d->trig;
+  const float rmin = d->r_min, rmax = d->r_max;
+
+  const int lcA = w * SO + 2 * lane - 2;  // tile column of the lane's first point
+  int jA = L.c0 + lcA, jB = jA + 1;       // scan columns
+  if (L.wrap) {
+    jA = wrap_col(jA, L.Ws);
+    jB = wrap_col(jB, L.Ws);
+  }
+  const bool okA = jA >= 0 && jA < L.Ws, okB = jB >= 0 && jB < L.Ws;
+  const unsigned offA = (unsigned)(okA ? jA : 0) * (unsigned)L.s, offB = (unsigned)(okB ? jB : 0) * (unsigned)L.s;
+  float spA = 0.f, cpA = 1.f, spB = 0.f, cpB = 1.f;
+  if (!XYZR) {
+    if (okA) sincosf(fmaf((float)(jA * L.s), d->daz, d->az0), &spA, &cpA);
+    if (okB) sincosf(fmaf((float)(jB * L.s), d->daz, d->az0), &spB, &cpB);
+  }
+  const bool strip = lane >= 1 && lane <= SO / 2;  // holds two of the strip's columns
+  const bool outA = strip && lcA < L.cn;            // first column is an output
+  const bool outB = strip && lcA + 1 < L.cn;        // second column is an output
+  const int rbase = L.r0 - 1, nsteps = L.rn + 3;
+  unsigned vout = (unsigned)L.r0 * (unsigned)L.Ws + (unsigned)(L.c0 + lcA);  // output vertex, tile row 0
+
+  auto fetch = [&](int q, int k) {
+    const long long ro = rows_s[k];
+    float4* sl = ring + (q & (RING - 1)) * 64;
+    const int i = rbase + k;
+    if (XYZR) {
+      fetch_point(sl, xyzr, nullptr, nullptr, i, ro, okA, offA, 0.f, 1.f);
+      fetch_point(sl + 32, xyzr, nullptr, nullptr, i, ro, okB, offB, 0.f, 1.f);
+    } else {
+      fetch_point(sl, nullptr, range, trig, i, ro, okA, offA, spA, cpA);
+      fetch_point(sl + 32, nullptr, range, trig, i, ro, okB, offB, spB, cpB);
+    }
+  };
+#pragma unroll
+  for (int q = 0; q < RING - 1; ++q) {
+    if (q < nsteps) fetch(q, q);
+    cp_async_commit();
+  }
+
+  const float2 Z2 = make_float2(0.f, 0.f);
+  const float QNAN = __int_as_float(0x7fc00000);
+  float2 ppx = Z2, ppy = Z2, ppz = Z2, ppr = make_float2(-1.f, -1.f);  // row k-1 (zeroed out of range)
+  float2 rx1 = Z2, ry1 = Z2, rz1 = Z2, lr1 = Z2;                        // R edges of row k-1
+  float2 ux = Z2, uy = Z2, uz = Z2;                // row k-1's normal sums: the terms above it
+  float2 nx2 = make_float2(QNAN, QNAN), ny2 = nx2, nz2 = nx2;  // normals of row k-2 (NaN: none)
+  uint32_t m2 = 0;   // mesh bytes of row k-2 (first | second << 8)
+  uint32_t win = 0;  // mesh bytes: row k-1 in bits 0-15, row k in bits 16-31
+
+  for (int hr = 0; hr < nsteps; ++hr) {
+    // row hr has landed once at most RING-2 newer groups are pending
+    cp_async_wait<RING - 2>();
+    const int slot = hr & (RING - 1);
+    const float4 PA = ring[slot * 64], PB = ring[slot * 64 + 32];
+    // refill the slot read one step ago with row hr+RING-1
+    if (hr + RING - 1 < nsteps) fetch(hr + RING - 1, hr + RING - 1);
+    cp_async_commit();
+
+    const bool vA = in_range(PA.w, rmin, rmax), vB = in_range(PB.w, rmin, rmax);
+    const float2 px = make_float2(vA ? PA.x : 0.f, vB ? PB.x : 0.f);
+    const float2 py = make_float2(vA ? PA.y : 0.f, vB ? PB.y : 0.f);
+    const float2 pz = make_float2(vA ? PA.z : 0.f, vB ? PB.z : 0.f);
+    const float2 pr = make_float2(PA.w, PB.w);
+    // right neighbours: the lane's second point and the next lane's first
+    const float2 qx = right_of(px), qy = right_of(py), qz = right_of(pz), qr = right_of(pr);
+    const bool vN = in_range(qr.y, rmin, rmax);
+    // R edges of row k
+    const float2 ex = sub2(qx, px), ey = sub2(qy, py), ez = sub2(qz, pz);
+    const float2 le = len2(ex, ey, ez);
+    const float2 jh = make_float2(d->jump_h, d->jump_h), jv = make_float2(d->jump_v, d->jump_v);
+    bool cA, cB;
+    jump_cut2(pr, qr, jh, cA, cB);
+    const bool RA = vA && vB && !cA, RB = vB && vN && !cB;
+    // D and G edges of row k-1
+    const bool vpA = win & B_VALID, vpB = (win >> 8) & B_VALID;
+    const float2 dx = sub2(px, ppx), dy = sub2(py, ppy), dz = sub2(pz, ppz);
+    const float2 gx = sub2(qx, ppx), gy = sub2(qy, ppy), gz = sub2(qz, ppz);
+    const float2 ld = len2(dx, dy, dz), lg = len2(gx, gy, gz);
+    bool dA, dB, gA, gB;
+    jump_cut2(ppr, pr, jv, dA, dB);
+    jump_cut2(ppr, qr, jv, gA, gB);
+    const bool DA = vpA && vA && !dA, DB = vpB && vB && !dB;
+    const bool GA = vpA && vB && !gA, GB = vpB && vN && !gB;
+    win |= ((DA ? B_D : 0u) | (GA ? B_G : 0u)) | (((DB ? B_D : 0u) | (GB ? B_G : 0u)) << 8) |
+           ((((RA ? B_R : 0u) | (vA ? B_VALID : 0u)) | (((RB ? B_R : 0u) | (vB ? B_VALID : 0u)) << 8)) << 16);
+    const uint32_t up = __shfl_up_sync(FULL, win, 1), dn = __shfl_down_sync(FULL, win, 1);
+    // the left neighbour's bytes (row k-1, row k) and the right neighbour's (row k-1)
+    const uint32_t m1A = win & 0xffu, m1B = (win >> 8) & 0xffu;
+    const uint32_t l1A = up >> 8 & 0xffu, l0A = up >> 24;  // left of the first column: previous lane's second
+    const uint32_t l1B = m1A;                              // left of the second: the first
+    const uint32_t r1B = dn & 0xffu;                       // right of the second: next lane's first
+    // R edges of row k-1 ending at each column (below: F of row k-1)
+    const float2 fx1 = left_of(rx1), fy1 = left_of(ry1), fz1 = left_of(rz1), lf1 = left_of(lr1);
+
+    // normals of row k-1: the three terms below it
+    float2 sx = ux, sy = uy, sz = uz;
+    tri2(dx, dy, dz, ld, gx, gy, gz, lg, DA && GA && RA, DB && GB && RB, sx, sy, sz);
+    tri2(gx, gy, gz, lg, rx1, ry1, rz1, lr1, GA && (m1A & B_R) && DB, GB && (m1B & B_R) && (r1B & B_D), sx, sy,
+         sz);
+    tri2(dx, dy, dz, ld, fx1, fy1, fz1, lf1, (l1A & B_R) && DA && (l1A & B_G), (l1B & B_R) && DB && (l1B & B_G),
+         sx, sy, sz);
+    const float2 q2 = fma2(sx, sx, fma2(sy, sy, mul2(sz, sz)));
+    // a sum shorter than 2^-63 counts as no normal (as does a zero sum)
+    const bool hA = (m1A & B_VALID) && q2.x >= FLT_MIN && q2.x < 3.0e38f;
+    const bool hB = (m1B & B_VALID) && q2.y >= FLT_MIN && q2.y < 3.0e38f;
+    const float nsign = d->nsign;
+    const float2 fn = make_float2(hA ? nsign * rsq_approx(q2.x) : QNAN, hB ? nsign * rsq_approx(q2.y) : QNAN);
+    const float2 nx1 = mul2(sx, fn), ny1 = mul2(sy, fn), nz1 = mul2(sz, fn);
+    const uint32_t m1 = (win & 0xffffu) | (hA ? (uint32_t)B_HASN : 0u) | (hB ? (uint32_t)B_HASN << 8 : 0u);
+
+    // normals of row k: the three terms above it
+    {
+      const float2 fx = left_of(ex), fy = left_of(ey), fz = left_of(ez), lf = left_of(le);
+      const float2 glx = left_of(gx), gly = left_of(gy), glz = left_of(gz), lgl = left_of(lg);
+      const bool DlA = l1A & B_D, DlB = DA;  // D edge of the left column, row k-1
+      const bool GlA = l1A & B_G, GlB = GA;  // G edge of the left column, row k-1
+      const bool RlA = l0A & B_R, RlB = RA;  // R edge of the left column, row k
+      ux = Z2;
+      uy = Z2;
+      uz = Z2;
+      tri2(dx, dy, dz, ld, ex, ey, ez, le, RA && DA && GA, RB && DB && GB, ux, uy, uz);
+      tri2(dx, dy, dz, ld, glx, gly, glz, lgl, DA && GlA && (l1A & B_R), DB && GlB && (l1B & B_R), ux, uy, uz);
+      tri2(glx, gly, glz, lgl, fx, fy, fz, lf, GlA && RlA && DlA, GlB && RlB && DlB, ux, uy, uz);
+    }
+
+    // homogeneity mask and outputs of row k-2
+    if (hr >= 3) {
+      const float cos_t = d->cos_t, ccx = d->comp_x, ccy = d->comp_y, ccz = d->comp_z;
+      const float2 nRx = right_of(nx2), nRy = right_of(ny2), nRz = right_of(nz2);
+      const float2 nGx = right_of(nx1), nGy = right_of(ny1), nGz = right_of(nz1);
+      bool hRA, hRB, hDA, hDB, hGA, hGB;
+      homog2<ANGLE>(nx2, ny2, nz2, nRx, nRy, nRz, cos_t, ccx, ccy, ccz, hRA, hRB);
+      homog2<ANGLE>(nx2, ny2, nz2, nx1, ny1, nz1, cos_t, ccx, ccy, ccz, hDA, hDB);
+      homog2<ANGLE>(nx2, ny2, nz2, nGx, nGy, nGz, cos_t, ccx, ccy, ccz, hGA, hGB);
+      const uint32_t m2A = m2 & 0xffu, m2B = m2 >> 8;
+      const uint32_t bA = m2A | (((m2A & B_R) && hRA) ? B_HR : 0u) | (((m2A & B_D) && hDA) ? B_HD : 0u) |
+                          (((m2A & B_G) && hGA) ? B_HG : 0u);
+      const uint32_t bB = m2B | (((m2B & B_R) && hRB) ? B_HR : 0u) | (((m2B & B_D) && hDB) ? B_HD : 0u) |
+                          (((m2B & B_G) && hGB) ? B_HG : 0u);
+      const int lr = hr - 3;
+      if (lr < L.rn) {
+        if (strip)
+          *reinterpret_cast<uint16_t*>(tb + lr * TC + lcA) =
+              (uint16_t)((outA ? bA : 0u) | (outB ? bB << 8 : 0u));
+        if (outA) {
+          const bool hasA = m2A & B_HASN, hasB = m2B & B_HASN;
+          const float oxA = hasA ? nx2.x : 0.f, oyA = hasA ? ny2.x : 0.f, ozA = hasA ? nz2.x : 0.f;
+          const float oxB = hasB ? nx2.y : 0.f, oyB = hasB ? ny2.y : 0.f, ozB = hasB ? nz2.y : 0.f;
+          uint8_t* mp = d->mb + vout;
+          float* np = d->nrm + 3 * (size_t)vout;
+          if (outB && ((reinterpret_cast<uintptr_t>(mp) & 1) == 0)) {
+            *reinterpret_cast<uint16_t*>(mp) = (uint16_t)(bA | (bB << 8));
+          } else {
+            mp[0] = (uint8_t)bA;
+            if (outB) mp[1] = (uint8_t)bB;
+          }
+          if (outB && ((reinterpret_cast<uintptr_t>(np) & 7) == 0)) {
+            float2* np2 = reinterpret_cast<float2*>(np);
+            np2[0] = make_float2(oxA, oyA);
+            np2[1] = make_float2(ozA, oxB);
+            np2[2] = make_float2(oyB, ozB);
+          } else {
+            np[0] = oxA;
+            np[1] = oyA;
+            np[2] = ozA;
+            if (outB) {
+              np[3] = oxB;
+              np[4] = oyB;
+              np[5] = ozB;
+            }
+          }
+        }
+      }
+      vout += (unsigned)L.Ws;
+    }
+
+    // rotate the window
+    win >>= 16;
+    m2 = m1;
+    ppx = px;
+    ppy = py;
+    ppz = pz;
+    ppr = pr;
+    rx1 = ex;
+    ry1 = ey;
+    rz1 = ez;
+    lr1 = le;
+    nx2 = nx1;
+    ny2 = ny1;
+    nz2 = nz1;
+  }
+  cp_async_wait_all();
+}
+
+// ---------------------------------------------------------------------------
+// tile components (Algorithm 1 restricted to the tile)
+// ---------------------------------------------------------------------------
+// Runs of a strip row.  Lanes 1..30 hold the strip's columns in pairs
+// (strip position 2*lane: the first, 2*lane+1: the second); linkA / linkB
+// are the homogeneous R edges first -> second and second -> next lane's
+// first.  Gives the strip positions of the first vertex of the runs that
+// hold the lane's two columns.
+__device__ __forceinline__ void run_starts(bool linkA, bool linkB, int lane, int& posA, int& posB) {
+  const unsigned LA = __ballot_sync(FULL, linkA), LB = __ballot_sync(FULL, linkB);
+  // lanes below this one that a run does not pass through (lane 0 never links)
+  const unsigned brk = (~(LA & LB) & ((1u << lane) - 1u)) | 1u;
+  const int m = 31 - __clz(brk);
+  posA = ((LB >> m) & 1u) ? 2 * m + 1 : 2 * m + 2;
+  posB = linkA ? posA : 2 * lane + 1;
+}
+
 template <int TR, int NW>
 __device__ __forceinline__ void tile_cross_and_roots(const Loc& L, const uint8_t* __restrict__ tb, int* lp,
                                                      uint16_t* __restrict__ lroot, int32_t* __restrict__ parent,
                                                      int32_t* err);
 
 // Tile components of the tile bytes tb[TR][TC] (mesh + homogeneity bits of
-// the tile's own vertices): horizontal runs from a ballot, vertical joins in a
-// shared-memory union-find, then joins across strips and the seam.  Writes
-// every vertex's tile-local root to lroot and marks each root in parent.
+// the tile's own vertices; zero outside the tile).  C1: each warp walks its
+// strip row by row; the horizontal runs come from two ballots, and only a
+// run's first vertex (plus the strip's and the tile's last column) enters
+// the shared-memory union-find.  A vertical edge is joined unless the
+// column to its left already joins the same two vertices (its D edge and
+// the two R edges, or its D edge and the lower R edge for a G edge).  Then
+// C2 / C3 (below).  Writes every vertex's tile-local root to lroot and marks
+// each root in parent.
+// Performs a warp's queued unions (pairs of tile-local indices), one per
+// lane at a time, then empties the queue.
+__device__ __forceinline__ void flush_unions(int* lp, const uint32_t* wq, int n, int limit, int32_t* err) {
+  __syncwarp();
+  for (int j = (int)(threadIdx.x & 31); j < n; j += 32) {
+    const uint32_t pr = wq[j];
+    union_sh(lp, (int)(pr & 0xffffu), (int)(pr >> 16), limit, err);
+  }
+  __syncwarp();
+}
+
+// Appends the pairs (a, b) of the lanes with f set to the warp's queue.
+__device__ __forceinline__ void queue_union(uint32_t* wq, int& qn, bool f, int a, int b) {
+  const unsigned m = __ballot_sync(FULL, f);
+  if (f) wq[qn + __popc(m & ((1u << (threadIdx.x & 31)) - 1u))] = (uint32_t)a | ((uint32_t)b << 16);
+  qn += __popc(m);
+}
+
+// Tile components of the tile bytes tb[TR][TC] (mesh + homogeneity bits of
+// the tile's own vertices; zero outside the tile).  C1: each warp walks its
+// strip row by row; the horizontal runs come from two ballots, and only a
+// run's first vertex (plus the strip's and the tile's last column) enters
+// the shared-memory union-find.  A vertical edge is joined unless the
+// column to its left already joins the same two vertices (its D edge and
+// the two R edges, or its D edge and the lower R edge for a G edge); the
+// joins wait in a per-warp queue and run 32 at a time.  Then C2 / C3
+// (below).  Writes every vertex's tile-local root to lroot and marks each
+// root in parent.
 template <int TR, int NW>
-__device__ __forceinline__ void tile_components(const Loc& L, const uint8_t* __restrict__ tb, int* lp,
-                                uint16_t* __restrict__ lroot, int32_t* __restrict__ parent,
-                                int32_t* err) {
+__device__ __forceinline__ void tile_components(const Loc& L, const uint8_t* __restrict__ tb, int* lp, uint32_t* q,
+                                                uint16_t* __restrict__ lroot, int32_t* __restrict__ parent,
+                                                int32_t* err) {
   using G = Geo<TR, NW>;
   constexpr int TC = G::TC;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int lcw = w * SO + lane - 1;  // this lane's tile column
-  const bool act = lane >= 1 && lane <= SO && lcw < L.cn;
-
-  // C1: each warp walks its strip row by row
-  uint8_t bprev = 0;
+  const int lcA = w * SO + 2 * lane - 2;       // tile column of the lane's first column
+  const int base = w * SO - 2;                 // tile column of strip position 0
+  const bool act = lane >= 1 && lane <= SO / 2;
+  const bool lead = lane == 0 && w > 0;        // reads the previous strip's last column
+  uint32_t* wq = q + w * QCAP;
+  int qn = 0;                                  // queued unions (warp-uniform)
+  uint32_t prev = 0;                           // previous row's bytes of the lane's columns
+  int psA = 0, psB = 0;                        // previous row's run starts (tile-linear)
   for (int lr = 0; lr < L.rn; ++lr) {
-    const uint8_t b = act ? tb[lr * TC + lcw] : 0;
-    const bool hr_in = act && lane < SO && lcw + 1 < L.cn && (b & B_HR);
-    const unsigned B = __ballot_sync(FULL, hr_in);
-    const unsigned brk = ~B & ((1u << lane) - 1u);  // lanes left of me whose R edge breaks the run
-    const int start = 32 - __clz(brk);              // first lane of my run (>= 1)
-    const int v = lr * TC + lcw;
-    if (act) lp[v] = lr * TC + (w * SO + start - 1);
-    __syncwarp();
-    if (act && lr > 0) {
-      const uint8_t bu = bprev;
-      const uint8_t bul = lane >= 2 ? tb[(lr - 1) * TC + lcw - 1] : 0;
-      const uint8_t bl = lane >= 2 ? tb[lr * TC + lcw - 1] : 0;
-      // D edge (lr-1, c) - (lr, c); implied when the left lane's D edge and
-      // both rows' R edges already join the same vertices
-      if (bu & B_HD) {
-        const bool implied = (bul & B_HD) && (bul & B_HR) && (bl & B_HR);
-        if (!implied) union_s(lp, v, v - TC, G::NV + 1, err);
-      }
-      // G edge (lr-1, c-1) - (lr, c)
-      if (bul & B_HG) {
-        const bool implied = (bul & B_HD) && (bl & B_HR);
-        if (!implied) union_s(lp, v, v - TC - 1, G::NV + 1, err);
-      }
+    uint32_t cur = 0;
+    if (act) cur = *reinterpret_cast<const uint16_t*>(tb + lr * TC + lcA);
+    else if (lead) cur = (uint32_t)tb[lr * TC + lcA + 1] << 8;
+    const uint32_t bA = cur & 0xffu, bB = cur >> 8;
+    const bool linkA = act && (bA & B_HR) && lcA + 1 < L.cn;
+    const bool linkB = act && lane < SO / 2 && (bB & B_HR) && lcA + 2 < L.cn;
+    int posA, posB;
+    run_starts(linkA, linkB, lane, posA, posB);
+    const int vA = lr * TC + lcA;
+    const int sA = lr * TC + base + posA, sB = lr * TC + base + posB;
+    if (act) {
+      if (posA == 2 * lane || lcA == L.cn - 1) lp[vA] = sA;
+      if (posB == 2 * lane + 1 || lane == SO / 2 || lcA + 1 == L.cn - 1) lp[vA + 1] = sB;
     }
-    __syncwarp();
-    bprev = b;
+    const uint32_t up = __shfl_up_sync(FULL, cur | (prev << 16), 1);
+    const int upsB = __shfl_up_sync(FULL, psB, 1);
+    bool fDA = false, fGA = false, fDB = false, fGB = false;
+    if (act && lr > 0) {
+      const uint32_t pA = prev & 0xffu, pB = prev >> 8;
+      const uint32_t lB = (up >> 8) & 0xffu, lpB = up >> 24;  // left column: this row, previous row
+      // first column (its left: the previous lane's second column, or the
+      // previous strip's last column for lane 1, whose G edge is a C2 edge)
+      fDA = (pA & B_HD) && !((lpB & B_HD) && (lpB & B_HR) && (lB & B_HR));
+      fGA = lane > 1 && (lpB & B_HG) && !((lpB & B_HD) && (lB & B_HR));
+      // second column (its left: the first)
+      fDB = (pB & B_HD) && !((pA & B_HD) && (pA & B_HR) && (bA & B_HR));
+      fGB = (pA & B_HG) && !((pA & B_HD) && (bA & B_HR));
+    }
+    queue_union(wq, qn, fDA, sA, psA);
+    queue_union(wq, qn, fGA, sA, upsB);
+    queue_union(wq, qn, fDB, sB, psB);
+    queue_union(wq, qn, fGB, sB, psA);
+    if (qn > QCAP - 4 * 32) {
+      flush_unions(lp, wq, qn, G::NV + 1, err);
+      qn = 0;
+    }
+    prev = cur;
+    psA = sA;
+    psB = sB;
   }
+  flush_unions(lp, wq, qn, G::NV + 1, err);
   __syncthreads();
   tile_cross_and_roots<TR, NW>(L, tb, lp, lroot, parent, err);
 }
 
-// C2: edges across strip borders, and the seam of a tile spanning the ring;
-// C3: every vertex's tile-local root (vertices out of range: NO_ROOT), roots
-// marked in the global union-find.
+// C2: edges across strip borders, and the seam of a tile spanning the ring
+// (from a strip's or the tile's last column, both kept in the union-find, to
+// a strip's first column or column 0, both run starts); C3: every vertex's
+// tile-local root (vertices out of range: NO_ROOT) from its run's first
+// vertex, roots marked in the global union-find.
 template <int TR, int NW>
 __device__ __forceinline__ void tile_cross_and_roots(const Loc& L, const uint8_t* __restrict__ tb, int* lp,
                                                      uint16_t* __restrict__ lroot, int32_t* __restrict__ parent,
@@ -363,220 +731,75 @@ __device__ __forceinline__ void tile_cross_and_roots(const Loc& L, const uint8_t
     }
     if (ac < 0) continue;
     const uint8_t bits = tb[lr * TC + ac];
-    if (bits & B_HR) union_s(lp, lr * TC + ac, lr * TC + bc, G::NV + 1, err);
-    if ((bits & B_HG) && lr + 1 < L.rn) union_s(lp, lr * TC + ac, (lr + 1) * TC + bc, G::NV + 1, err);
+    if (bits & B_HR) union_sh(lp, lr * TC + ac, lr * TC + bc, G::NV + 1, err);
+    if ((bits & B_HG) && lr + 1 < L.rn) union_sh(lp, lr * TC + ac, (lr + 1) * TC + bc, G::NV + 1, err);
   }
   __syncthreads();
 
-  // C3: roots (vertices out of range: 0xFFFF)
-  for (int lr = w; lr < L.rn; lr += NW) {
-    for (int lc = lane; lc < L.cn; lc += 32) {
-      const int v = lr * TC + lc;
-      const size_t gv = (size_t)(L.r0 + lr) * L.Ws + (L.c0 + lc);
-      const size_t gr = (size_t)(L.r0 + lr) * root_pitch(L.Ws) + (L.c0 + lc);
-      if (!(tb[v] & B_VALID)) {
-        lroot[gr] = NO_ROOT;
-        continue;
-      }
-      const int r = find_s(lp, v, G::NV + 1);
-      lroot[gr] = (uint16_t)r;
-      if (r == v) parent[gv] = (int32_t)gv;
+  // C3: each warp over its strip's rows
+  const int lcA = w * SO + 2 * lane - 2;
+  const bool act = lane >= 1 && lane <= SO / 2;
+  const size_t pitch = root_pitch(L.Ws);
+  for (int lr = 0; lr < L.rn; ++lr) {
+    const uint32_t cur = act ? *reinterpret_cast<const uint16_t*>(tb + lr * TC + lcA) : 0u;
+    const uint32_t bA = cur & 0xffu, bB = cur >> 8;
+    const bool linkA = act && (bA & B_HR) && lcA + 1 < L.cn;
+    const bool linkB = act && lane < SO / 2 && (bB & B_HR) && lcA + 2 < L.cn;
+    int posA, posB;
+    run_starts(linkA, linkB, lane, posA, posB);
+    const int vA = lr * TC + lcA;
+    int rA = 0, rB = 0;
+    if (act && posA == 2 * lane) rA = find_sh(lp, vA, G::NV + 1);
+    if (act && posB == 2 * lane + 1) rB = find_sh(lp, vA + 1, G::NV + 1);
+    const uint32_t pub = (uint32_t)rA | ((uint32_t)rB << 16);
+    const uint32_t gA = __shfl_sync(FULL, pub, posA >> 1), gB = __shfl_sync(FULL, pub, posB >> 1);
+    if (act && lcA < L.cn) {
+      const uint32_t RA = (posA & 1) ? (gA >> 16) : (gA & 0xffffu);
+      const uint32_t RB = (posB & 1) ? (gB >> 16) : (gB & 0xffffu);
+      const bool valA = bA & B_VALID, valB = bB & B_VALID;
+      const size_t gi = (size_t)(L.r0 + lr);
+      *reinterpret_cast<uint32_t*>(lroot + gi * pitch + (L.c0 + lcA)) =
+          (valA ? RA : (uint32_t)NO_ROOT) | ((valB ? RB : (uint32_t)NO_ROOT) << 16);
+      const size_t gv = gi * L.Ws + (L.c0 + lcA);
+      if (valA && RA == (uint32_t)vA) parent[gv] = (int32_t)gv;
+      if (valB && RB == (uint32_t)(vA + 1)) parent[gv + 1] = (int32_t)(gv + 1);
     }
   }
 }
 
-// ---------------------------------------------------------------------------
-// k_tile: decode + mesh + normals + edge mask + tile components
-// ---------------------------------------------------------------------------
 // One tile of one scan: decode + mesh + normals + edge mask + tile
 // components (smem: Geo<TR,NW>::bytes of dynamic shared memory).
 template <int TR, int NW>
 __device__ __forceinline__ void tile_body(const ScanDesc* d, int lt, unsigned char* smem, int32_t* err) {
   using G = Geo<TR, NW>;
-  constexpr int TC = G::TC;
-  int* lp = reinterpret_cast<int*>(smem + G::off_lp);
-  uint8_t* tb = smem + G::off_tb;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  float4* ring = reinterpret_cast<float4*>(smem + G::off_ring) + (size_t)w * (RING + 1) * 32 + lane;
-  const Loc L = make_loc(d, lt, TR, TC);
-  const float4* __restrict__ xyzr = d->xyzr;
-  const float* __restrict__ range = d->range;
-  const int32_t* __restrict__ order = d->order;
-  const float2* __restrict__ trig = d->trig;
-  const float rmin = d->r_min, rmax = d->r_max, jh = d->jump_h, jv = d->jump_v;
+  const Loc L = make_loc(d, lt, TR, G::TC);
   // offsets of the input rows the tile reads (ring order applied once)
   long long* rows_s = reinterpret_cast<long long*>(smem + G::off_rows);
   for (int k = threadIdx.x; k < L.rn + 3; k += G::NT) {
     const int i = L.r0 - 1 + k;
     long long ro = -1;
     if (i >= 0 && i < L.H) {
-      const int row = __ldg(order + i);
+      const int row = __ldg(d->order + i);
       if ((unsigned)row < (unsigned)L.H) ro = (long long)row * L.W;
     }
     rows_s[k] = ro;
   }
   __syncthreads();
-
-  // The sweep: warp w owns tile columns w*29-1 .. w*29+30 (one per lane),
-  // of which lanes 1..29 are its output columns.  Each lane streams its
-  // column's rows from global memory into its own ring of shared-memory
-  // slots with cp.async, RING rows ahead of use (coalesced 16-byte copies
-  // across the warp; a lane only reads slots it filled, so no barrier).  At
-  // step hr it holds scan row r0-1+hr and completes: the R edge of that row,
-  // the D and G edges of the row above, the normal of the row above that
-  // (Sec. 2, normal estimation) and the homogeneity mask of the row above
-  // that (Algorithm 1 predicate).
-  {
-    const int col = w * SO + lane;  // tile column + 1
-    const int lc = col - 1;         // tile column
-    const bool out_col = lane >= 1 && lane <= SO && lc < L.cn;
-    int j = L.c0 + lc;              // scan column of this lane
-    if (L.wrap) {
-      if (j < 0) j += L.Ws;
-      else if (j >= L.Ws) j -= L.Ws;
-      if (j >= L.Ws) j %= L.Ws;
-    }
-    const bool colok = j >= 0 && j < L.Ws;
-    const size_t coff = (size_t)(colok ? j : 0) * L.s;
-    float sp = 0.f, cp = 1.f;
-    if (!xyzr && colok) sincosf(fmaf((float)(j * L.s), d->daz, d->az0), &sp, &cp);
-    const float nsign = d->nsign, cos_t = d->cos_t;
-    const float cx = d->comp_x, cy = d->comp_y, cz = d->comp_z;
-    const bool angle_pred = d->pred == LSG_PRED_ANGLE;
-    uint8_t* __restrict__ mb_out = d->mb;
-    float* __restrict__ nrm_out = d->nrm;
-
-    float4 Pp = make_float4(0.f, 0.f, 0.f, -1.f);           // row k-1
-    float eRx_p = 0.f, eRy_p = 0.f, eRz_p = 0.f, LR_p = 0.f;  // R edge of row k-1
-    float eDx_pp = 0.f, eDy_pp = 0.f, eDz_pp = 0.f, LD_pp = 0.f;  // D edge of row k-2
-    float eGx_ppL = 0.f, eGy_ppL = 0.f, eGz_ppL = 0.f, LG_ppL = 0.f;  // G edge of row k-2, left lane
-    uint32_t m_pp = 0, m_p = 0;                                // mesh bits of rows k-2, k-1
-    float4 n_pp = make_float4(0.f, 0.f, 0.f, 0.f);             // normal of row k-2
-    const int rbase = L.r0 - 1;
-    const int nsteps = L.rn + 3;
-    size_t vout = (size_t)L.r0 * L.Ws + (size_t)(L.c0 + lc);  // output vertex of tile row 0
-#pragma unroll
-    for (int q = 0; q < RING; ++q) {
-      if (q < nsteps) fetch_point(ring + q * 32, xyzr, range, trig, rbase + q, rows_s[q], colok, coff, sp, cp);
-      asm volatile("cp.async.commit_group;\n" ::: "memory");
-    }
-
-    for (int hr = 0; hr < nsteps; ++hr) {
-      // row hr has landed once at most RING-1 newer groups are pending
-      asm volatile("cp.async.wait_group %0;\n" ::"n"(RING - 1) : "memory");
-      float4 P = ring[(hr % (RING + 1)) * 32];
-      // refill: the slot of row hr+RING was last read one step ago
-      if (hr + RING < nsteps)
-        fetch_point(ring + ((hr + RING) % (RING + 1)) * 32, xyzr, range, trig, rbase + hr + RING,
-                    rows_s[hr + RING], colok, coff, sp, cp);
-      asm volatile("cp.async.commit_group;\n" ::: "memory");
-      if (!in_range(P.w, rmin, rmax)) P = make_float4(0.f, 0.f, 0.f, P.w);  // finite spokes only
-      float4 Pr;
-      Pr.x = __shfl_down_sync(FULL, P.x, 1);
-      Pr.y = __shfl_down_sync(FULL, P.y, 1);
-      Pr.z = __shfl_down_sync(FULL, P.z, 1);
-      Pr.w = __shfl_down_sync(FULL, P.w, 1);
-      const bool vP = in_range(P.w, rmin, rmax);
-      const bool vPr = lane < 31 && in_range(Pr.w, rmin, rmax);
-      // R edge of row k
-      const bool Rk = vP && vPr && !jump_cut(P.w, Pr.w, jh);
-      const float eRx = Pr.x - P.x, eRy = Pr.y - P.y, eRz = Pr.z - P.z;
-      const float LR = vlen(eRx, eRy, eRz);
-      // D and G edges of row k-1
-      const bool vPp = in_range(Pp.w, rmin, rmax);
-      const bool Dk1 = vPp && vP && !jump_cut(Pp.w, P.w, jv);
-      const bool Gk1 = vPp && vPr && !jump_cut(Pp.w, Pr.w, jv);
-      const float eDx = P.x - Pp.x, eDy = P.y - Pp.y, eDz = P.z - Pp.z;
-      const float eGx = Pr.x - Pp.x, eGy = Pr.y - Pp.y, eGz = Pr.z - Pp.z;
-      const float LD = vlen(eDx, eDy, eDz), LG = vlen(eGx, eGy, eGz);
-      m_p |= (Dk1 ? B_D : 0u) | (Gk1 ? B_G : 0u);
-      const uint32_t m_k = (Rk ? B_R : 0u) | (vP ? B_VALID : 0u);
-      // neighbours' mesh bits (byte 0: row k-2, byte 1: row k-1, byte 2: row k)
-      const uint32_t word = m_pp | (m_p << 8) | (m_k << 16);
-      const uint32_t up = __shfl_up_sync(FULL, word, 1);
-      const uint32_t dn = __shfl_down_sync(FULL, word, 1);
-      const float eRxL = __shfl_up_sync(FULL, eRx_p, 1);
-      const float eRyL = __shfl_up_sync(FULL, eRy_p, 1);
-      const float eRzL = __shfl_up_sync(FULL, eRz_p, 1);
-      const float LRL = __shfl_up_sync(FULL, LR_p, 1);
-
-      // normal of row k-1, vertex p (spokes in the paper's order A..F):
-      // A = eD, B = eG, C = eR(k-1), D = -eD(k-2), E = -eG(k-2, left),
-      // F = -eR(k-1, left); triangle (p, q, q') counts when its 3 edges exist
-      float4 n_p = make_float4(0.f, 0.f, 0.f, 0.f);
-      {
-        const uint32_t upp = up & 0xff, upl = (up >> 8) & 0xff, dnl = (dn >> 8) & 0xff;
-        const bool sA = Dk1, sB = Gk1, sC = (m_p & B_R) != 0, sD = (m_pp & B_D) != 0;
-        const bool sE = (upp & B_G) != 0, sF = (upl & B_R) != 0;
-        float sx = 0.f, sy = 0.f, sz = 0.f;
-        tri_term(eDx, eDy, eDz, LD, eGx, eGy, eGz, LG, sA && sB && Rk, sx, sy, sz);
-        tri_term(eGx, eGy, eGz, LG, eRx_p, eRy_p, eRz_p, LR_p, sB && sC && (dnl & B_D), sx, sy, sz);
-        tri_term(eRx_p, eRy_p, eRz_p, LR_p, -eDx_pp, -eDy_pp, -eDz_pp, LD_pp, sC && sD && (m_pp & B_G), sx, sy,
-                 sz);
-        tri_term(-eDx_pp, -eDy_pp, -eDz_pp, LD_pp, -eGx_ppL, -eGy_ppL, -eGz_ppL, LG_ppL,
-                 sD && sE && (upp & B_R), sx, sy, sz);
-        tri_term(-eGx_ppL, -eGy_ppL, -eGz_ppL, LG_ppL, -eRxL, -eRyL, -eRzL, LRL, sE && sF && (upp & B_D), sx, sy,
-                 sz);
-        tri_term(-eRxL, -eRyL, -eRzL, LRL, eDx, eDy, eDz, LD, sF && sA && (upl & B_G), sx, sy, sz);
-        const float q2 = fmaf(sx, sx, fmaf(sy, sy, sz * sz));
-        // q2 > 0 only when some triangle counted (absent terms are exact zeros)
-        if ((m_p & B_VALID) && q2 > 0.f && q2 < 3.0e38f) {
-          const float f = nsign * rsqrtf(q2);
-          n_p = make_float4(sx * f, sy * f, sz * f, 1.f);
-        }
-      }
-
-      // homogeneity mask and outputs of row k-2
-      if (hr >= 3) {
-        const float4 nr_pp = make_float4(__shfl_down_sync(FULL, n_pp.x, 1), __shfl_down_sync(FULL, n_pp.y, 1),
-                                         __shfl_down_sync(FULL, n_pp.z, 1), __shfl_down_sync(FULL, n_pp.w, 1));
-        const float4 nr_p = make_float4(__shfl_down_sync(FULL, n_p.x, 1), __shfl_down_sync(FULL, n_p.y, 1),
-                                        __shfl_down_sync(FULL, n_p.z, 1), __shfl_down_sync(FULL, n_p.w, 1));
-        const int lr = hr - 3;
-        uint32_t bits = m_pp | (n_pp.w != 0.f ? B_HASN : 0u);
-        bits |= ((m_pp & B_R) && homog(n_pp, nr_pp, angle_pred, cos_t, cx, cy, cz)) ? B_HR : 0u;
-        bits |= ((m_pp & B_D) && homog(n_pp, n_p, angle_pred, cos_t, cx, cy, cz)) ? B_HD : 0u;
-        bits |= ((m_pp & B_G) && homog(n_pp, nr_p, angle_pred, cos_t, cx, cy, cz)) ? B_HG : 0u;
-        if (out_col && lr < L.rn) {
-          const size_t v = vout;
-          mb_out[v] = (uint8_t)bits;
-          nrm_out[3 * v + 0] = n_pp.x;
-          nrm_out[3 * v + 1] = n_pp.y;
-          nrm_out[3 * v + 2] = n_pp.z;
-          tb[lr * TC + lc] = (uint8_t)bits;
-        }
-        vout += L.Ws;
-      }
-
-      // rotate the window
-      const float gxL = __shfl_up_sync(FULL, eGx, 1), gyL = __shfl_up_sync(FULL, eGy, 1);
-      const float gzL = __shfl_up_sync(FULL, eGz, 1), gLL = __shfl_up_sync(FULL, LG, 1);
-      m_pp = m_p;
-      m_p = m_k;
-      eDx_pp = eDx;
-      eDy_pp = eDy;
-      eDz_pp = eDz;
-      LD_pp = LD;
-      eGx_ppL = gxL;
-      eGy_ppL = gyL;
-      eGz_ppL = gzL;
-      LG_ppL = gLL;
-      eRx_p = eRx;
-      eRy_p = eRy;
-      eRz_p = eRz;
-      LR_p = LR;
-      n_pp = n_p;
-      Pp = P;
-    }
+  const bool angle = d->pred == LSG_PRED_ANGLE;
+  if (d->xyzr) {
+    if (angle) tile_sweep<TR, NW, true, true>(d, L, smem);
+    else tile_sweep<TR, NW, false, true>(d, L, smem);
+  } else {
+    if (angle) tile_sweep<TR, NW, true, false>(d, L, smem);
+    else tile_sweep<TR, NW, false, false>(d, L, smem);
   }
   __syncthreads();
-
-  // tile components (Algorithm 1 restricted to the tile)
-  tile_components<TR, NW>(L, tb, lp, d->lroot, d->parent, err);
+  tile_components<TR, NW>(L, smem + G::off_tb, reinterpret_cast<int*>(smem + G::off_lp),
+                          reinterpret_cast<uint32_t*>(smem + G::off_q), d->lroot, d->parent, err);
 }
 
 template <int TR, int NW>
-__global__ void __launch_bounds__(NW * 32, 24 / NW) k_tile(const __grid_constant__ KArgs a) {
+__global__ void __launch_bounds__(NW * 32, 16 / NW) k_tile(const __grid_constant__ KArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
     int lt;
@@ -595,7 +818,8 @@ __global__ void __launch_bounds__(NW * 32) k_tile_ccl(const __grid_constant__ KA
   constexpr int TC = G::TC;
   extern __shared__ __align__(16) unsigned char smem[];
   int* lp = reinterpret_cast<int*>(smem);
-  uint8_t* tb = smem + sizeof(int) * G::NV;
+  uint8_t* tb = smem + G::lp_bytes;
+  uint32_t* q = reinterpret_cast<uint32_t*>(smem + G::lp_bytes + ((G::NV + 15) / 16) * 16);
   for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
     int lt;
     const ScanDesc* d = tile_desc(a, t, lt);
@@ -605,7 +829,7 @@ __global__ void __launch_bounds__(NW * 32) k_tile_ccl(const __grid_constant__ KA
       tb[k] = (lr < L.rn && lc < L.cn) ? d->mb[(size_t)(L.r0 + lr) * L.Ws + (L.c0 + lc)] : 0;
     }
     __syncthreads();
-    tile_components<TR, NW>(L, tb, lp, d->lroot, d->parent, a.err);
+    tile_components<TR, NW>(L, tb, lp, q, d->lroot, d->parent, a.err);
     __syncthreads();
   }
 }
@@ -978,10 +1202,10 @@ static cudaError_t set_attrs() {
 cudaError_t prepare_kernels() {
   cudaError_t e;
   if ((e = set_attrs<16, 4>()) != cudaSuccess) return e;
+  if ((e = set_attrs<32, 2>()) != cudaSuccess) return e;
   if ((e = set_attrs<32, 4>()) != cudaSuccess) return e;
   if ((e = set_attrs<32, 8>()) != cudaSuccess) return e;
   if ((e = set_attrs<64, 4>()) != cudaSuccess) return e;
-  if ((e = set_attrs<64, 8>()) != cudaSuccess) return e;
   return cudaSuccess;
 }
 
@@ -993,10 +1217,10 @@ cudaError_t launch_prep(const KArgs& a, cudaStream_t st) {
 
 #define LSG_DISPATCH(tile, FN, ...)                       \
   switch (tile) {                                         \
-    case LSG_TILE_32x116: return FN<32, 4>(__VA_ARGS__);  \
-    case LSG_TILE_32x232: return FN<32, 8>(__VA_ARGS__);  \
-    case LSG_TILE_64x116: return FN<64, 4>(__VA_ARGS__);  \
-    case LSG_TILE_64x232: return FN<64, 8>(__VA_ARGS__);  \
+    case LSG_TILE_32x120: return FN<32, 2>(__VA_ARGS__);  \
+    case LSG_TILE_32x240: return FN<32, 4>(__VA_ARGS__);  \
+    case LSG_TILE_32x480: return FN<32, 8>(__VA_ARGS__);  \
+    case LSG_TILE_64x240: return FN<64, 4>(__VA_ARGS__);  \
     default: return FN<16, 4>(__VA_ARGS__);               \
   }
 

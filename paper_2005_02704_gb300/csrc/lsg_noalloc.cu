@@ -78,7 +78,7 @@ extern "C" lsg_status lsg_segment_noalloc(const lsg_scan* scan, const lsg_params
   lsg::KArgs a;
   memset(&a, 0, sizeof(a));
   a.one = lsg::make_desc(scan, params, out, Ws);
-  lsg::set_tiles(a.one, LSG_TILE_16x116, 0);
+  lsg::set_tiles(a.one, LSG_TILE_16x240, 0);
   a.one.order = reinterpret_cast<int32_t*>(base + kOrderOff);
   a.one.trig = reinterpret_cast<float2*>(base + kTrigOff);
   a.one.parent = reinterpret_cast<int32_t*>(base + kParentOff);
@@ -90,8 +90,8 @@ extern "C" lsg_status lsg_segment_noalloc(const lsg_scan* scan, const lsg_params
   // everything else is fully written by the kernels before it is read.
   cudaError_t e = cudaMemsetAsync(a.err, 0, sizeof(int32_t), cs);
   if (e == cudaSuccess) e = lsg::launch_prep(a, cs);
-  if (e == cudaSuccess) e = lsg::launch_tile(LSG_TILE_16x116, a, cs);
-  if (e == cudaSuccess) e = lsg::launch_merge(LSG_TILE_16x116, a, cs);
-  if (e == cudaSuccess) e = lsg::launch_flatten(LSG_TILE_16x116, a, cs);
+  if (e == cudaSuccess) e = lsg::launch_tile(LSG_TILE_16x240, a, cs);
+  if (e == cudaSuccess) e = lsg::launch_merge(LSG_TILE_16x240, a, cs);
+  if (e == cudaSuccess) e = lsg::launch_flatten(LSG_TILE_16x240, a, cs);
   return e == cudaSuccess ? LSG_OK : LSG_E_CUDA;
 }

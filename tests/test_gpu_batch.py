@@ -56,7 +56,7 @@ def mixed_specs(n, seed0):
 
 
 @pytest.mark.parametrize("fused", [True, False], ids=["fused", "phased"])
-@pytest.mark.parametrize("tile", ["16x116", "32x116", "32x232", "64x116", "64x232"])
+@pytest.mark.parametrize("tile", ["16x240", "32x120", "32x240", "32x480", "64x240"])
 def test_batch_equals_per_scan(ctx, tile, fused):
     lsg, _ = mods()
     specs = mixed_specs(12, 5000)

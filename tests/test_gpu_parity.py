@@ -55,7 +55,7 @@ def run_gpu(ctx, scan, p, range_only=False, tile=None):
     torch.cuda.synchronize()
     assert ctx.error() == lsg.LSG_OK
     if tile is not None:
-        lsg.lsg_set_tile(ctx.h, lsg.TILES["16x116"])
+        lsg.lsg_set_tile(ctx.h, lsg.TILES["16x240"])
     return (out.meshbits.cpu().numpy(), out.normals.cpu().numpy(), out.labels.cpu().numpy(),
             int(out.nseg.cpu()[0]))
 
@@ -111,10 +111,12 @@ def test_component_predicate(ctx):
 
 RAGGED = [
     # (rings, cols, s, wrap, tile)
-    (1, 1, 1, 1, "16x116"), (1, 7, 1, 1, "16x116"), (2, 2, 1, 1, "16x116"), (3, 3, 1, 1, "64x232"),
-    (9, 131, 1, 1, "16x116"), (9, 131, 1, 0, "16x116"), (17, 257, 2, 1, "32x232"), (17, 257, 3, 0, "32x116"),
-    (5, 1030, 1, 1, "64x116"), (33, 129, 1, 1, "64x232"), (16, 1800, 5, 1, "16x116"), (7, 1000, 15, 1, "32x232"),
-    (64, 300, 1, 1, "32x116"), (3, 512, 2, 1, "64x116"), (24, 640, 4, 0, "64x232"),
+    (1, 1, 1, 1, "16x240"), (1, 7, 1, 1, "16x240"), (2, 2, 1, 1, "16x240"), (3, 3, 1, 1, "64x240"),
+    (9, 131, 1, 1, "32x120"), (9, 131, 1, 0, "32x120"), (17, 257, 2, 1, "32x480"), (17, 257, 3, 0, "32x120"),
+    (5, 1030, 1, 1, "32x240"), (33, 129, 1, 1, "64x240"), (16, 1800, 5, 1, "16x240"), (7, 1000, 15, 1, "32x480"),
+    (64, 300, 1, 1, "32x120"), (3, 512, 2, 1, "32x240"), (24, 640, 4, 0, "64x240"),
+    (8, 240, 1, 1, "16x240"), (8, 241, 1, 1, "16x240"), (5, 481, 1, 1, "32x480"), (3, 61, 1, 1, "32x120"),
+    (35, 121, 1, 0, "32x120"),
 ]
 
 
@@ -194,14 +196,14 @@ def test_label_from_mask_random_masks(ctx):
             flat[hom] |= hb
         mb = flat.reshape(H, Ws)
         want, nwant = O.label_from_mask(mb, valid_full, W, s, wrap)
-        for tile in ("16x116", "64x116", "32x232"):
+        for tile in ("16x240", "32x120", "32x480"):
             lsg.lsg_set_tile(ctx.h, lsg.TILES[tile])
             got, n = ctx.label_from_mask(torch.from_numpy(mb).to(dev), torch.from_numpy(valid_full).to(dev), W, s,
                                          wrap)
             torch.cuda.synchronize()
             assert np.array_equal(got.cpu().numpy(), want), (case, H, W, s, wrap, tile)
             assert int(n.cpu()[0]) == nwant
-    lsg.lsg_set_tile(ctx.h, lsg.TILES["16x116"])
+    lsg.lsg_set_tile(ctx.h, lsg.TILES["16x240"])
 
 
 def test_nan_elevation_is_flagged_not_faulted(ctx):
