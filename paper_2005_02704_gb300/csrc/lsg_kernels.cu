@@ -952,26 +952,31 @@ __device__ __forceinline__ int32_t backfill(int32_t lo, int dlo, int32_t hi, int
   return first != -1 ? first : second;
 }
 
-// Per tile: (1) stage the tile's 16-bit local roots in shared memory,
-// (2) resolve every local root once to its global root and label (and count
-// the global roots), (3) write every point's label, back-filling the points
-// between sampled columns.  Loops are two-dimensional (warps over rows,
-// lanes over columns): no integer division per point.
+// Per tile: (1) stage the tile's 16-bit local roots in shared memory four
+// at a time and list the tile-local roots, (2) resolve every local root
+// once to its global root and label (and count the global roots), (3) write
+// every point's label, back-filling the points between sampled columns.
 template <int TR, int NW>
 struct FlatGeo {
   static constexpr int TC = NW * SO, NV = TR * TC;
+  static constexpr int NQ = TC / 4;                                         // root quads per tile row
   static constexpr size_t off_lr = 0;                                      // uint16 [NV] tile roots
   static constexpr size_t off_lab = ((sizeof(uint16_t) * NV + 15) / 16) * 16;  // int32 [NV] root labels
   static constexpr size_t off_list = off_lab + sizeof(int32_t) * NV;       // uint16 [NV] list of roots
   static constexpr size_t bytes = off_list + ((sizeof(uint16_t) * NV + 15) / 16) * 16;
 };
 
+__device__ __forceinline__ int32_t root_label(const int32_t* lab_s, uint32_t r) {
+  return r == NO_ROOT ? -1 : lab_s[r];
+}
+
 // Labels of one tile (NTB threads; fsm: FlatGeo<TR,NW>::bytes of dynamic
 // shared memory; nlist: a shared counter).
 template <int TR, int NW, int NTB>
 __device__ __forceinline__ void flatten_body(const ScanDesc* d, int lt, unsigned char* fsm, int& nlist) {
   using FG = FlatGeo<TR, NW>;
-  constexpr int TC = FG::TC, NWF = NTB / 32;
+  constexpr int TC = FG::TC, NQ = FG::NQ, NWF = NTB / 32;
+  static_assert(TC % 4 == 0, "tile rows are read as quads of roots");
   uint16_t* lr_s = reinterpret_cast<uint16_t*>(fsm + FG::off_lr);
   int32_t* lab_s = reinterpret_cast<int32_t*>(fsm + FG::off_lab);
   uint16_t* list_s = reinterpret_cast<uint16_t*>(fsm + FG::off_list);
@@ -983,31 +988,58 @@ __device__ __forceinline__ void flatten_body(const ScanDesc* d, int lt, unsigned
   int32_t* __restrict__ labels = d->labels;
   const int limit = L.H * Ws + 1;
   if (tid == 0) nlist = 0;
-  // (1) the tile's roots, four at a time (rows are 8-byte aligned: the
-  //     pitch is a multiple of 8 and TC a multiple of 4)
-  const int nq = (L.cn + 3) >> 2;
-  for (int lr = wf; lr < L.rn; lr += NWF) {
-    const uint2* src = reinterpret_cast<const uint2*>(lroot + (size_t)(L.r0 + lr) * root_pitch(Ws) + L.c0);
-    uint2* dst = reinterpret_cast<uint2*>(lr_s + lr * TC);
-#pragma unroll 2
-    for (int q = lane; q < nq; q += 32) dst[q] = __ldg(src + q);
-  }
   __syncthreads();
-  // (2) list the tile-local roots, then resolve each to its global root,
-  //     four chains per thread at a time
-  for (int lr = wf; lr < L.rn; lr += NWF) {
-    for (int lc0 = 0; lc0 < L.cn; lc0 += 32) {
-      const int lc = lc0 + lane;
-      const int v = lr * TC + lc;
-      const bool is_root = lc < L.cn && lr_s[v] == v;
-      const unsigned m = __ballot_sync(FULL, is_root);
-      int base = 0;
-      if (lane == 0 && m) base = atomicAdd(&nlist, __popc(m));
-      base = __shfl_sync(FULL, base, 0);
-      if (is_root) list_s[base + __popc(m & ((1u << lane) - 1u))] = (uint16_t)v;
+  // (1) the tile's roots, four at a time (rows are 8-byte aligned: the pitch
+  //     is a multiple of 8 and TC a multiple of 4); the roots among them are
+  //     appended to the list (one atomic per warp and pass)
+  const int nquad = L.rn * NQ, nq = (L.cn + 3) >> 2;
+  for (int k0 = 0; k0 < nquad; k0 += NTB) {
+    const int k = k0 + tid;
+    const int lr = k / NQ, q = k - (k / NQ) * NQ;
+    const int v0 = lr * TC + 4 * q;
+    uint32_t m = 0;  // which of the four are roots
+    if (k < nquad) {
+      uint2 r4 = make_uint2(0xFFFFFFFFu, 0xFFFFFFFFu);
+      if (q < nq) r4 = __ldg(reinterpret_cast<const uint2*>(lroot + (size_t)(L.r0 + lr) * root_pitch(Ws) + L.c0) + q);
+      // entries past the tile's last column (the next tile's, or the row
+      // padding, which nothing writes) are staged as NO_ROOT
+      const int lim = L.cn - 4 * q;  // columns of the quad inside the tile
+      if (lim < 4) {
+        if (lim <= 0) {
+          r4 = make_uint2(0xFFFFFFFFu, 0xFFFFFFFFu);
+        } else if (lim == 1) {
+          r4.x |= 0xFFFF0000u;
+          r4.y = 0xFFFFFFFFu;
+        } else if (lim == 2) {
+          r4.y = 0xFFFFFFFFu;
+        } else {
+          r4.y |= 0xFFFF0000u;
+        }
+      }
+      *reinterpret_cast<uint2*>(lr_s + v0) = r4;
+      m = ((r4.x & 0xffffu) == (uint32_t)v0) | (((r4.x >> 16) == (uint32_t)(v0 + 1)) << 1) |
+          (((r4.y & 0xffffu) == (uint32_t)(v0 + 2)) << 2) | (((r4.y >> 16) == (uint32_t)(v0 + 3)) << 3);
+    }
+    const int c = __popc(m);
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(FULL, incl, o);
+      if (lane >= o) incl += t;
+    }
+    int base = 0;
+    if (lane == 31 && incl) base = atomicAdd(&nlist, incl);
+    base = __shfl_sync(FULL, base, 31);
+    int pos = base + incl - c;
+    while (m) {
+      const int j = __ffs(m) - 1;
+      list_s[pos++] = (uint16_t)(v0 + j);
+      m &= m - 1;
     }
   }
   __syncthreads();
+  // (2) resolve each listed root to its global root, four chains per thread
+  //     at a time (independent loads in flight)
   int nroots = 0;
   const int nl = nlist;
   for (int k0 = tid; k0 < nl; k0 += 4 * NTB) {
@@ -1021,7 +1053,6 @@ __device__ __forceinline__ void flatten_body(const ScanDesc* d, int lt, unsigned
       gv[q] = (L.r0 + v / TC) * Ws + L.c0 + v % TC;
       x[q] = gv[q];
     }
-    // walk the four chains together (independent loads in flight)
     for (int it = 0; it < limit; ++it) {
       bool more = false;
 #pragma unroll
@@ -1047,13 +1078,23 @@ __device__ __forceinline__ void flatten_body(const ScanDesc* d, int lt, unsigned
   const int cnt = __reduce_add_sync(FULL, nroots);
   if (lane == 0 && cnt) atomicAdd(d->nseg, cnt);
   __syncthreads();
+  // (3) labels
   if (s == 1) {
-    for (int lr = wf; lr < L.rn; lr += NWF) {
-      int32_t* dst = labels + (size_t)(L.r0 + lr) * W + L.c0;
-#pragma unroll 4
-      for (int lc = lane; lc < L.cn; lc += 32) {
-        const uint16_t r = lr_s[lr * TC + lc];
-        dst[lc] = r == NO_ROOT ? -1 : lab_s[r];
+    for (int k = tid; k < nquad; k += NTB) {
+      const int lr = k / NQ, q = k - (k / NQ) * NQ;
+      const int lc = 4 * q;
+      if (lc >= L.cn) continue;
+      const uint2 r4 = *reinterpret_cast<const uint2*>(lr_s + lr * TC + lc);
+      const int4 o = make_int4(root_label(lab_s, r4.x & 0xffffu), root_label(lab_s, r4.x >> 16),
+                               root_label(lab_s, r4.y & 0xffffu), root_label(lab_s, r4.y >> 16));
+      int32_t* dst = labels + (size_t)(L.r0 + lr) * W + L.c0 + lc;
+      if (lc + 4 <= L.cn && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+        *reinterpret_cast<int4*>(dst) = o;
+      } else {
+        dst[0] = o.x;
+        if (lc + 1 < L.cn) dst[1] = o.y;
+        if (lc + 2 < L.cn) dst[2] = o.z;
+        if (lc + 3 < L.cn) dst[3] = o.w;
       }
     }
   } else {
@@ -1062,8 +1103,7 @@ __device__ __forceinline__ void flatten_body(const ScanDesc* d, int lt, unsigned
       const int row = d->order[i];
       for (int lc = lane; lc < L.cn; lc += 32) {
         const int j = L.c0 + lc;
-        const uint16_t rl = lr_s[lr * TC + lc];
-        const int32_t lo = rl == NO_ROOT ? -1 : lab_s[rl];
+        const int32_t lo = root_label(lab_s, lr_s[lr * TC + lc]);
         labels[(size_t)i * W + (size_t)j * s] = lo;
         // the s-1 points after column j*s
         int jh = -1, cnext = 0;
@@ -1077,8 +1117,7 @@ __device__ __forceinline__ void flatten_body(const ScanDesc* d, int lt, unsigned
         int32_t hi = -1;
         if (jh >= 0) {
           if (jh >= L.c0 && jh < L.c0 + L.cn) {
-            const uint16_t rh = lr_s[lr * TC + (jh - L.c0)];
-            hi = rh == NO_ROOT ? -1 : lab_s[rh];
+            hi = root_label(lab_s, lr_s[lr * TC + (jh - L.c0)]);
           } else {
             hi = vertex_label_global<TR, TC>(lroot, parent, Ws, W, s, i, jh, limit);
           }
