@@ -10,7 +10,9 @@ is needed between steps.
 
 The JSON line reports points/s of the batched path (value), the same metric
 end to end through the C ABI with host buffers (e2e: host->device copy of the
-inputs, the pass, device->host copy of labels and segment counts), the plain
+inputs, the pass, device->host copy of labels and segment counts, in chunks
+whose copies overlap the other chunks' passes; the one-after-the-other
+variant is reported beside it), the plain
 per-scan path (one lsg_segment call per scan), the dominant kernel's HBM
 roofline fraction, and the FP64 oracle timed on the host cores on a bounded
 sample (cpu_baseline).
@@ -64,6 +66,7 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--phased", action="store_true", help="force four phased launches (else the autotuner's choice)")
     ap.add_argument("--fused", action="store_true", help="force the single persistent launch")
+    ap.add_argument("--e2e-chunks", type=int, default=16, help="chunks of the pipelined end-to-end path")
     ap.add_argument("--tile", default=None, help="force a tile shape (e.g. 32x240) instead of autotuning")
     ap.add_argument("--serve-scale", type=float, default=10.0,
                     help="time compression of the 60 s sensor trace for the served measurement")
@@ -354,6 +357,25 @@ def main():
     phase = [x / nrep for x in phase]
 
     # ---- end to end through the C ABI with host buffers --------------------
+    # (a) the pipelined host path: chunks of scans whose copies in both
+    #     directions overlap the other chunks' passes; (b) for reference, the
+    #     same copies and the single-plan pass queued one after the other
+    pipe = db.pipeline(ctx, plan.tile, chunks=args.e2e_chunks, fused=plan.fused)
+    for _ in range(max(args.warmup, 3)):
+        pipe.step(stream)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    h2d = d2h = 0
+    for _ in range(args.steps):
+        h2d, d2h = pipe.step(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_e2e = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+    e2e_value = pts_all / (ms_e2e / 1e3)
+    pipe.close()
     for _ in range(max(args.warmup, 3)):
         db.upload()
         plan.run()
@@ -362,16 +384,14 @@ def main():
     barrier()
     torch.cuda.synchronize()
     e0.record(stream)
-    h2d = d2h = 0
     for _ in range(args.steps):
-        h2d = db.upload()
+        db.upload()
         plan.run()
-        d2h = db.download()
+        db.download()
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
-    ms_e2e = max_over_ranks(e0.elapsed_time(e1) / args.steps)
-    e2e_value = pts_all / (ms_e2e / 1e3)
+    ms_e2e_serial = max_over_ranks(e0.elapsed_time(e1) / args.steps)
 
     # ---- plain per-scan path: one lsg_segment call per scan ----------------
     plain = None
@@ -454,7 +474,9 @@ def main():
                           {"ring_order": phase[0], "tile": phase[1], "merge": phase[2], "labels": phase[3]}),
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "ms_per_step": ms_e2e},
+                    "ms_per_step": ms_e2e, "path": f"HostPipeline, {args.e2e_chunks} chunks, 3 streams",
+                    "serial_ms_per_step": ms_e2e_serial,
+                    "serial_value": pts_all / (ms_e2e_serial / 1e3)},
             "plain": plain,
             "served": served,
             "scans_per_s": db.n * world / (ms_step / 1e3),

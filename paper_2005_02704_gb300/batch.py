@@ -6,7 +6,9 @@ aligned per scan) plus one buffer of elevations; all outputs in one buffer per
 kind.  ``lsg_scan`` / ``lsg_out`` descriptors point into them, so one
 ``lsg_batch_plan`` covers the whole batch and replays stay valid as long as
 the buffers live.  A pinned host mirror of the inputs and of the labels and
-segment counts serves the end-to-end (host -> device -> host) measurement.
+segment counts serves the end-to-end (host -> device -> host) path, which
+``HostPipeline`` runs in chunks so that copies in both directions overlap the
+passes.
 """
 from __future__ import annotations
 
@@ -131,6 +133,10 @@ class DeviceBatch:
     def plan(self, ctx: "lsg.Context", tile: int = lsg.LSG_TILE_AUTO) -> "lsg.BatchPlan":
         return lsg.BatchPlan(ctx, self.c_scans(), self.c_params(), self.c_outs(), tile)
 
+    def pipeline(self, ctx: "lsg.Context", tile: int = lsg.LSG_TILE_AUTO, chunks: int = 8,
+                 fused=None) -> "HostPipeline":
+        return HostPipeline(self, ctx, tile, chunks, fused)
+
     # ---- per-scan views of the device outputs -----------------------------
     def view(self, b: int):
         sh = self.shapes[b]
@@ -144,6 +150,78 @@ class DeviceBatch:
         p0, p1 = int(self.pt_off[b]), int(self.pt_off[b + 1])
         e0, e1 = int(self.e_off[b]), int(self.e_off[b + 1])
         return self.d_elev[e0:e1], self.d_xyzr[p0:p1].view(sh.rings, sh.cols, 4)
+
+
+class HostPipeline:
+    """End-to-end passes from the pinned host mirror, in chunks that overlap.
+
+    The batch is cut into ``chunks`` runs of consecutive scans with about
+    equal point counts, each with its own captured plan.  In a step, chunk c's
+    inputs go host -> device on one stream, its pass runs on a second stream
+    once they have landed, and its labels and segment counts go device ->
+    host on a third once the pass is done, so the copies of the neighbouring
+    chunks, in both directions, run under each chunk's pass.  A step starts
+    after the work already queued on the caller's stream and the caller's
+    stream waits for its last copy.
+    """
+
+    def __init__(self, db: DeviceBatch, ctx: "lsg.Context", tile: int = lsg.LSG_TILE_AUTO, chunks: int = 8,
+                 fused=None):
+        torch = db.torch
+        self.db = db
+        n = db.n
+        chunks = max(1, min(int(chunks), n))
+        bounds = [0]
+        for c in range(1, chunks):
+            b = int(np.searchsorted(db.pt_off, db.points * c / chunks))
+            b = max(bounds[-1] + 1, min(b, n - (chunks - c)))
+            bounds.append(b)
+        bounds.append(n)
+        self.ranges = [(b0, b1) for b0, b1 in zip(bounds[:-1], bounds[1:]) if b1 > b0]
+        scans, params, outs = db.c_scans(), db.c_params(), db.c_outs()
+        self.plans = [lsg.BatchPlan(ctx, scans[b0:b1], params[b0:b1], outs[b0:b1], tile) for b0, b1 in self.ranges]
+        if fused is not None:
+            for p in self.plans:
+                p.set_fused(bool(fused))
+        self.s_in = torch.cuda.Stream(db.dev)
+        self.s_run = torch.cuda.Stream(db.dev)
+        self.s_out = torch.cuda.Stream(db.dev)
+        self.ev_in = [torch.cuda.Event() for _ in self.ranges]
+        self.ev_run = [torch.cuda.Event() for _ in self.ranges]
+        self.ev_out = torch.cuda.Event()
+
+    def step(self, stream=None):
+        """One end-to-end pass; returns (host->device bytes, device->host bytes)."""
+        torch, db = self.db.torch, self.db
+        cur = stream if stream is not None else torch.cuda.current_stream(db.dev)
+        self.s_in.wait_stream(cur)
+        self.s_run.wait_stream(cur)
+        self.s_out.wait_stream(cur)
+        with torch.cuda.stream(self.s_in):
+            db.d_elev.copy_(db.h_elev, non_blocking=True)
+        h2d, d2h = db.h_elev.numel() * 4, 0
+        for c, (b0, b1) in enumerate(self.ranges):
+            p0, p1 = int(db.pt_off[b0]), int(db.pt_off[b1])
+            with torch.cuda.stream(self.s_in):
+                db.d_xyzr[p0:p1].copy_(db.h_xyzr[p0:p1], non_blocking=True)
+                self.ev_in[c].record(self.s_in)
+            self.s_run.wait_event(self.ev_in[c])
+            self.plans[c].run(stream=self.s_run)
+            self.ev_run[c].record(self.s_run)
+            self.s_out.wait_event(self.ev_run[c])
+            with torch.cuda.stream(self.s_out):
+                db.h_lab[p0:p1].copy_(db.d_lab[p0:p1], non_blocking=True)
+                db.h_nseg[b0:b1].copy_(db.d_nseg[b0:b1], non_blocking=True)
+            h2d += (p1 - p0) * 16
+            d2h += (p1 - p0) * 4 + (b1 - b0) * 4
+        self.ev_out.record(self.s_out)
+        cur.wait_event(self.ev_out)
+        return h2d, d2h
+
+    def close(self) -> None:
+        for p in self.plans:
+            p.close()
+        self.plans = []
 
 
 class _null:

@@ -132,3 +132,30 @@ def test_bench_workload_512_scans(ctx):
             nrm = nrm_all[v0:v0 + H * Ws].reshape(H, Ws, 3)
             parity.compare_geometry(mb, nrm, orc, parity.oracle_params(p), bounds)
     plan.close()
+
+
+@pytest.mark.parametrize("chunks", [1, 3, 8])
+def test_host_pipeline_equals_plan(ctx, chunks):
+    """The chunked end-to-end host path gives the single plan's labels and
+    segment counts in the pinned host buffers."""
+    lsg, _ = mods()
+    specs = mixed_specs(10, 7000)
+    scans = [lidarsim.make_scan(sp) for sp in specs]
+    db = make_batch(specs, scans)
+    plan = db.plan(ctx, lsg.TILES["32x120"])
+    plan.set_fused(False)
+    plan.run()
+    torch.cuda.synchronize()
+    want_lab, want_nseg = db.d_lab.cpu().clone(), db.d_nseg.cpu().clone()
+    db.d_lab.fill_(-7)
+    db.d_nseg.fill_(-7)
+    pipe = db.pipeline(ctx, lsg.TILES["32x120"], chunks=chunks, fused=False)
+    assert len(pipe.ranges) == min(chunks, db.n)
+    assert pipe.ranges[0][0] == 0 and pipe.ranges[-1][1] == db.n
+    h2d, d2h = pipe.step()
+    torch.cuda.synchronize()
+    assert ctx.error() == lsg.LSG_OK
+    assert h2d == db.points * 16 + db.h_elev.numel() * 4 and d2h == db.points * 4 + db.n * 4
+    assert torch.equal(db.h_lab, want_lab) and torch.equal(db.h_nseg, want_nseg)
+    pipe.close()
+    plan.close()
