@@ -64,6 +64,7 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-generator", action="store_true", help="skip timing the GPU scan generator")
     ap.add_argument("--phased", action="store_true", help="force four phased launches (else the autotuner's choice)")
     ap.add_argument("--fused", action="store_true", help="force the single persistent launch")
     ap.add_argument("--e2e-chunks", type=int, default=16, help="chunks of the pipelined end-to-end path")
@@ -284,6 +285,45 @@ def serve_measurement(args, local, world, max_over_ranks, sum_over_ranks):
             "pool_peak_bytes": pool_peak, "batches": nb, "mean_batch": mean_batch}
 
 
+def generator_measurement(specs, local, steps, warmup, max_over_ranks, sum_over_ranks):
+    """The GPU scan generator (lsg_raycast) producing the whole batch: one
+    launch per scan into a scratch buffer, timed with CUDA events."""
+    import numpy as np
+    import torch
+
+    import lidarsim
+    from paper_2005_02704_gb300 import lsg
+    dev = torch.device("cuda", local)
+    jobs, total = [], 0
+    for sp in specs:
+        elev = torch.tensor([math.radians(e) for e in sp.elev_deg], dtype=torch.float32, device=dev)
+        prims = torch.from_numpy(lidarsim.scene_prims(sp)).to(dev)
+        jobs.append((sp, elev, prims, total))
+        total += sp.rings * sp.cols
+    xyzr = torch.empty((total, 4), dtype=torch.float32, device=dev)
+    gt = torch.empty(total, dtype=torch.int32, device=dev)
+
+    def once():
+        for sp, elev, prims, off in jobs:
+            n = sp.rings * sp.cols
+            lsg.raycast(elev, sp.cols, float(np.float32(sp.az0)), float(np.float32(sp.daz)), prims, sp.sigma,
+                        sp.p_drop, sp.r_max, sp.seed, xyzr=xyzr[off:off + n].view(sp.rings, sp.cols, 4),
+                        gt=gt[off:off + n].view(sp.rings, sp.cols))
+
+    for _ in range(warmup):
+        once()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        once()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1) / steps)
+    return {"path": "lsg_raycast, one launch per scan (the batch's scenes, rays and noise)",
+            "ms_per_batch": ms, "rays_per_s": sum_over_ranks(total) / (ms / 1e3), "launches_per_batch": len(jobs)}
+
+
 # --------------------------------------------------------------------------
 # GPU arm
 # --------------------------------------------------------------------------
@@ -423,6 +463,10 @@ def main():
 
     # ---- served path: continuous batching of 8 sensors vs a serial loop ---
     served = None
+    generator = None
+    if not args.no_generator:
+        generator = generator_measurement(specs, local, max(3, min(args.steps, 5)), 2, max_over_ranks,
+                                          sum_over_ranks)
     if not args.no_serve:
         served = serve_measurement(args, local, world, max_over_ranks, sum_over_ranks)
 
@@ -479,6 +523,7 @@ def main():
                     "serial_value": pts_all / (ms_e2e_serial / 1e3)},
             "plain": plain,
             "served": served,
+            "generator": generator,
             "scans_per_s": db.n * world / (ms_step / 1e3),
             "gpu_launches": (1 if fused else 4) * args.steps,
             "clocks": clk,

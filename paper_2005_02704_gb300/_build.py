@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "liblsg.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["lsg_kernels.cu", "lsg_api.cu", "lsg_noalloc.cu", "lsg_post.cu"]
+SOURCES = ["lsg_kernels.cu", "lsg_api.cu", "lsg_noalloc.cu", "lsg_post.cu", "lsg_raycast.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-Xcompiler", "-fno-strict-aliasing"]

@@ -51,6 +51,17 @@ class lsg_host_io(ctypes.Structure):
                 ("nseg", ctypes.c_void_p), ("meshbits", ctypes.c_void_p), ("normals", ctypes.c_void_p)]
 
 
+class lsg_raycast_spec(ctypes.Structure):
+    _fields_ = [("rings", ctypes.c_int32), ("cols", ctypes.c_int32), ("elevation", ctypes.c_void_p),
+                ("azimuth0", ctypes.c_float), ("azimuth_step", ctypes.c_float), ("nprims", ctypes.c_int32),
+                ("prims", ctypes.c_void_p), ("sigma", ctypes.c_double), ("p_drop", ctypes.c_double),
+                ("r_max", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
+LSG_RAYCAST_MAX_PRIMS = 256
+LSG_PRIM_PLANE, LSG_PRIM_BOX, LSG_PRIM_CYL = 0, 1, 2
+
+
 class LsgError(RuntimeError):
     def __init__(self, status: int, what: str):
         super().__init__(f"{what}: {lsg_status_str(status)} ({status})")
@@ -94,6 +105,7 @@ def load(build: bool = True):
             "lsg_segment_stats": (ctypes.c_int, [_P, I32, I32, I32, I32, _P, _P, _P, _P, _P, _P, _P]),
             "lsg_segment_noalloc": (ctypes.c_int, [ctypes.POINTER(lsg_scan), ctypes.POINTER(lsg_params),
                                                    ctypes.POINTER(lsg_out), _P]),
+            "lsg_raycast": (ctypes.c_int, [ctypes.POINTER(lsg_raycast_spec), _P, _P, _P]),
             "lsg_default_params": (None, [ctypes.POINTER(lsg_params)]),
             "lsg_status_str": (ctypes.c_char_p, [ctypes.c_int]),
         }
@@ -224,6 +236,11 @@ def lsg_segment_noalloc(scan: lsg_scan, params: lsg_params, out: lsg_out, stream
     callers that may not allocate device memory.  Returns the status code."""
     return load().lsg_segment_noalloc(ctypes.byref(scan), ctypes.byref(params), ctypes.byref(out),
                                       stream or None)
+
+
+def lsg_raycast(spec: lsg_raycast_spec, xyzr: int, gt: int, stream: int = 0) -> int:
+    """Ray-casts one synthetic scan into device buffers; returns the status."""
+    return load().lsg_raycast(ctypes.byref(spec), xyzr, gt or None, stream or None)
 
 
 # ---- convenience layer (torch for device memory and streams) -------------
@@ -412,3 +429,27 @@ class BatchPlan:
             self.close()
         except Exception:
             pass
+
+
+def raycast(elev, cols: int, az0: float, daz: float, prims, sigma: float, p_drop: float, r_max: float, seed: int,
+            xyzr=None, gt=None, stream=None):
+    """Synthetic scan on the device (lsg_raycast): elev a float32 device
+    tensor [H] (radians), prims a float64 device tensor [n, 10]; returns
+    (xyzr [H, W, 4] float32, gt [H, W] int32) device tensors."""
+    import torch
+    H = int(elev.shape[0])
+    dev = elev.device
+    if xyzr is None:
+        xyzr = torch.empty((H, cols, 4), dtype=torch.float32, device=dev)
+    if gt is None:
+        gt = torch.empty((H, cols), dtype=torch.int32, device=dev)
+    spec = lsg_raycast_spec()
+    spec.rings, spec.cols = H, cols
+    spec.elevation = elev.data_ptr() if H else None
+    spec.azimuth0, spec.azimuth_step = az0, daz
+    spec.nprims = int(prims.shape[0])
+    spec.prims = prims.data_ptr() if spec.nprims else None
+    spec.sigma, spec.p_drop, spec.r_max = sigma, p_drop, r_max
+    spec.seed = seed & 0xFFFFFFFFFFFFFFFF
+    _check(lsg_raycast(spec, xyzr.data_ptr(), gt.data_ptr(), _stream_ptr(stream)), "lsg_raycast")
+    return xyzr, gt
