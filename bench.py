@@ -65,6 +65,7 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-generator", action="store_true", help="skip timing the GPU scan generator")
+    ap.add_argument("--no-spin", action="store_true", help="skip the streaming (per-packet) latency measurement")
     ap.add_argument("--phased", action="store_true", help="force four phased launches (else the autotuner's choice)")
     ap.add_argument("--fused", action="store_true", help="force the single persistent launch")
     ap.add_argument("--e2e-chunks", type=int, default=16, help="chunks of the pipelined end-to-end path")
@@ -324,6 +325,51 @@ def generator_measurement(specs, local, steps, warmup, max_over_ranks, sum_over_
             "ms_per_batch": ms, "rays_per_s": sum_over_ranks(total) / (ms / 1e3), "launches_per_batch": len(jobs)}
 
 
+def spin_measurement(local, tile, reps=20, packets=16):
+    """Streaming: a 128 x 4096 scan (the 128-ring template, 0.088 deg) pushed
+    in `packets` column ranges; device time from the last packet to labels
+    ready (the finish, which takes the last packet's columns too) against
+    one lsg_segment pass of the whole scan.  Medians over `reps`."""
+    import torch
+
+    import lidarsim
+    from paper_2005_02704_gb300 import lsg
+    dev = torch.device("cuda", local)
+    spec = lidarsim.ring128()
+    scan = lidarsim.make_scan(spec)
+    p = lsg.Params(r_max=spec.r_max, jump_rel_h=spec.jump_rel_h, jump_rel_v=spec.jump_rel_v,
+                   angle_rad=math.radians(spec.angle_deg))
+    elev = torch.from_numpy(scan.elev).to(dev)
+    xyzr = torch.from_numpy(scan.xyzr).to(dev)
+    ctx = lsg.Context(local, tile=tile)
+    out = lsg.alloc_outputs(scan.rings, scan.cols, 1, dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    full, last = [], []
+    for k in range(reps + 3):
+        torch.cuda.synchronize()
+        e0.record()
+        ctx.segment(elev, xyzr=xyzr, az0=scan.az0, daz=scan.daz, params=p, out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        if k >= 3:
+            full.append(e0.elapsed_time(e1))
+        spin = lsg.Spin(ctx, elev, xyzr=xyzr, az0=scan.az0, daz=scan.daz, params=p, out=out)
+        for q in range(1, packets):
+            spin.push(scan.cols * q // packets)
+        torch.cuda.synchronize()
+        e0.record()
+        spin.finish()  # the last packet is in place: finish takes the rest
+        e1.record()
+        torch.cuda.synchronize()
+        spin.close()
+        if k >= 3:
+            last.append(e0.elapsed_time(e1))
+    ctx.close()
+    f, l = statistics.median(full), statistics.median(last)
+    return {"scan": f"{scan.rings}x{scan.cols} (128-ring template), {packets} packets", "tile": tile,
+            "after_last_packet_ms": l, "full_pass_ms": f, "latency_cut": f / l}
+
+
 # --------------------------------------------------------------------------
 # GPU arm
 # --------------------------------------------------------------------------
@@ -463,6 +509,9 @@ def main():
 
     # ---- served path: continuous batching of 8 sensors vs a serial loop ---
     served = None
+    spin = None
+    if not args.no_spin and rank == 0:
+        spin = spin_measurement(local, plan.tile)
     generator = None
     if not args.no_generator:
         generator = generator_measurement(specs, local, max(3, min(args.steps, 5)), 2, max_over_ranks,
@@ -524,6 +573,7 @@ def main():
             "plain": plain,
             "served": served,
             "generator": generator,
+            "streaming": spin,
             "scans_per_s": db.n * world / (ms_step / 1e3),
             "gpu_launches": (1 if fused else 4) * args.steps,
             "clocks": clk,

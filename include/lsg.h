@@ -40,6 +40,7 @@ extern "C" {
 
 typedef struct lsg_ctx lsg_ctx;
 typedef struct lsg_plan lsg_plan;
+typedef struct lsg_spin lsg_spin;
 typedef void* lsg_stream; /* cudaStream_t */
 
 typedef enum {
@@ -317,6 +318,40 @@ lsg_status lsg_get_error(lsg_ctx* ctx);
 lsg_status lsg_segment_stats(lsg_ctx* ctx, int32_t H, int32_t W, int32_t s, int32_t min_points,
                              int32_t* labels, const float* normals, const uint8_t* meshbits, int32_t* sizes,
                              float* nsum, int32_t* nseg, lsg_stream stream);
+
+/* ---- Streaming: one revolution segmented while its columns arrive ----
+ *
+ * The paper builds the mesh while the sensor spins (Sec. 2, meshing; Fig. 1:
+ * the first stage can run with the scanning).  These calls do the per-tile
+ * work of lsg_segment column by column as the revolution arrives, so that
+ * after the last column only the first tile column (whose left neighbours
+ * are the revolution's last columns, across the seam), the joins that touch
+ * it and the labels remain.  The outputs equal lsg_segment's bit for bit.
+ *
+ * lsg_spin_begin   scan, params, out as for lsg_segment; the elevations must
+ *                  be in place, the x,y,z,r (or range) columns may still be
+ *                  arriving.  Allocates the spin's own workspace (counted
+ *                  against the context's budget: LSG_E_BUDGET) with the
+ *                  context's tile shape, computes the ring order and zeroes
+ *                  *nseg on `stream`.  *spin receives the handle.
+ * lsg_spin_push    columns [0, cols_ready) of the scan's input (full
+ *                  resolution, in firing order) are in place in device
+ *                  memory, ordered before this call on `stream` (e.g. by
+ *                  copies on it).  Launches the tiles whose columns, and the
+ *                  two sampled columns to their right, are all in place, and
+ *                  the joins between computed tile columns.  cols_ready must
+ *                  not decrease and not exceed cols (LSG_E_ARG).
+ * lsg_spin_finish  the whole revolution is in place: computes the rest; the
+ *                  outputs are valid once `stream` reaches this point.
+ *                  LSG_E_ARG if already finished.
+ * lsg_spin_destroy frees the spin (synchronises the device).
+ * Calls on one spin must be ordered on one stream; pushes after the finish
+ * return LSG_E_ARG. */
+lsg_status lsg_spin_begin(lsg_ctx* ctx, const lsg_scan* scan, const lsg_params* params, const lsg_out* out,
+                          lsg_spin** spin, lsg_stream stream);
+lsg_status lsg_spin_push(lsg_spin* spin, int32_t cols_ready, lsg_stream stream);
+lsg_status lsg_spin_finish(lsg_spin* spin, lsg_stream stream);
+lsg_status lsg_spin_destroy(lsg_spin* spin);
 
 /* Largest scan (rings x sampled columns) lsg_segment_noalloc accepts. */
 #define LSG_NOALLOC_MAX_VERTICES (1 << 20)

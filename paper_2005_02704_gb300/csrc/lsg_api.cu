@@ -769,4 +769,158 @@ lsg_status lsg_plan_destroy(lsg_plan* plan) {
   return LSG_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// streaming: one revolution segmented while its columns arrive
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+struct lsg_spin {
+  lsg_ctx* ctx = nullptr;
+  int tile = 0;
+  KArgs a;                    // a.one: the scan, with this spin's own workspace
+  void* ws = nullptr;         // workspace, then the tile lists
+  size_t bytes = 0;
+  int32_t* d_cols = nullptr;  // [tiles_c][tiles_r] local tile indices by tile column: 1, 2, .., last, 0
+  int cols_seen = 0;          // full-resolution columns in place
+  int done_to = 1;            // tile columns [1, done_to) computed (column 0 waits for the seam)
+  int merged_to = 1;          // tile columns [1, merged_to) joined to their right neighbours
+  int finished = 0;
+};
+
+namespace {
+
+// Launches k_tile or k_merge over the tile columns at positions [q0, q1) of
+// the spin's column order (1, 2, .., last, 0).
+cudaError_t spin_launch(const lsg_spin* sp, bool merge, int q0, int q1, cudaStream_t cs) {
+  if (q1 <= q0) return cudaSuccess;
+  KArgs a = sp->a;
+  a.tile_list = sp->d_cols + (size_t)q0 * a.one.tiles_r;
+  a.ntiles = (q1 - q0) * a.one.tiles_r;
+  return merge ? launch_merge(sp->tile, a, cs) : launch_tile(sp->tile, a, cs);
+}
+
+}  // namespace
+
+extern "C" {
+
+lsg_status lsg_spin_begin(lsg_ctx* ctx, const lsg_scan* scan, const lsg_params* params, const lsg_out* out,
+                          lsg_spin** spin, lsg_stream stream) {
+  if (!ctx || !spin) return LSG_E_ARG;
+  *spin = nullptr;
+  int Ws = 0;
+  lsg_status st = check_scan(scan, params, out, &Ws);
+  if (st != LSG_OK) return st;
+  DeviceGuard g(ctx->device);
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+  lsg_spin* sp = new (std::nothrow) lsg_spin();
+  if (!sp) return LSG_E_OOM;
+  sp->ctx = ctx;
+  sp->tile = ctx->tile;
+  memset(&sp->a, 0, sizeof(sp->a));
+  sp->a.one = make_desc(scan, params, out, Ws);
+  set_tiles(sp->a.one, sp->tile, 0);
+  sp->a.nscans = 1;
+  sp->a.err = ctx->d_err;
+  ScanDesc& d = sp->a.one;
+  if (scan->rings == 0 || scan->cols == 0) {
+    const cudaError_t e = cudaMemsetAsync(out->nseg, 0, sizeof(int32_t), cs);
+    if (e != cudaSuccess) {
+      delete sp;
+      return cuda_status(e);
+    }
+    *spin = sp;
+    return LSG_OK;
+  }
+  const size_t wsb = align_up(scan_ws_bytes(d.H, Ws), 256);
+  const size_t ntiles = (size_t)d.tiles_r * d.tiles_c;
+  const size_t bytes = wsb + sizeof(int32_t) * ntiles;
+  if (ctx->budget && ctx->used + bytes > ctx->budget) {
+    delete sp;
+    return LSG_E_BUDGET;
+  }
+  cudaError_t e = cudaMalloc(&sp->ws, bytes);
+  if (e != cudaSuccess) {
+    delete sp;
+    return cuda_status(e);
+  }
+  sp->bytes = bytes;
+  ctx->used += bytes;
+  carve_ws(d, static_cast<char*>(sp->ws));
+  sp->d_cols = reinterpret_cast<int32_t*>(static_cast<char*>(sp->ws) + wsb);
+  std::vector<int32_t> cols(ntiles);
+  for (int q = 0; q < d.tiles_c; ++q) {
+    const int tc = (q + 1) % d.tiles_c;  // position q holds tile column q+1; the last position column 0
+    for (int tr = 0; tr < d.tiles_r; ++tr) cols[(size_t)q * d.tiles_r + tr] = tr * d.tiles_c + tc;
+  }
+  e = cudaMemcpy(sp->d_cols, cols.data(), sizeof(int32_t) * ntiles, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = launch_prep(sp->a, cs);
+  if (e != cudaSuccess) {
+    lsg_spin_destroy(sp);
+    return cuda_status(e);
+  }
+  *spin = sp;
+  return LSG_OK;
+}
+
+lsg_status lsg_spin_push(lsg_spin* sp, int32_t cols_ready, lsg_stream stream) {
+  if (!sp || sp->finished) return LSG_E_ARG;
+  const ScanDesc& d = sp->a.one;
+  if (cols_ready < sp->cols_seen || cols_ready > d.W) return LSG_E_ARG;
+  sp->cols_seen = cols_ready;
+  if (d.H == 0 || d.W == 0) return LSG_OK;
+  DeviceGuard g(sp->ctx->device);
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+  const int TC = tile_shape(sp->tile).cols;
+  const int jr = (cols_ready + d.s - 1) / d.s;  // sampled columns in place
+  // tile column t needs its sampled columns and two to the right (the last
+  // one: the first two, around the seam, or none)
+  int t_end = sp->done_to;
+  while (t_end < d.tiles_c && jr >= std::min((t_end + 1) * TC + 2, d.Ws)) ++t_end;
+  cudaError_t e = spin_launch(sp, false, sp->done_to - 1, t_end - 1, cs);
+  if (e != cudaSuccess) return cuda_status(e);
+  sp->done_to = std::max(sp->done_to, t_end);
+  // tile column t joins its right neighbour once both are computed; the last
+  // column (right neighbour across the seam: column 0) waits for the finish
+  const int m_end = std::min(sp->done_to - 1, d.tiles_c - 1);
+  e = spin_launch(sp, true, sp->merged_to - 1, m_end - 1, cs);
+  if (e != cudaSuccess) return cuda_status(e);
+  sp->merged_to = std::max(sp->merged_to, m_end);
+  return LSG_OK;
+}
+
+lsg_status lsg_spin_finish(lsg_spin* sp, lsg_stream stream) {
+  if (!sp || sp->finished) return LSG_E_ARG;
+  sp->finished = 1;
+  const ScanDesc& d = sp->a.one;
+  sp->cols_seen = d.W;
+  if (d.H == 0 || d.W == 0) return LSG_OK;
+  DeviceGuard g(sp->ctx->device);
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+  // the remaining tile columns and column 0 (the tail of the column
+  // order), then their joins, then labels: three launches
+  cudaError_t e = spin_launch(sp, false, sp->done_to - 1, d.tiles_c, cs);
+  if (e == cudaSuccess) e = spin_launch(sp, true, sp->merged_to - 1, d.tiles_c, cs);
+  sp->done_to = sp->merged_to = d.tiles_c;
+  if (e == cudaSuccess) {
+    KArgs a = sp->a;
+    a.tile_list = nullptr;
+    a.ntiles = d.tiles_r * d.tiles_c;
+    e = launch_flatten(sp->tile, a, cs);
+  }
+  return cuda_status(e);
+}
+
+lsg_status lsg_spin_destroy(lsg_spin* sp) {
+  if (!sp) return LSG_E_ARG;
+  if (sp->ws) {
+    DeviceGuard g(sp->ctx->device);
+    cudaDeviceSynchronize();
+    cudaFree(sp->ws);
+    sp->ctx->used -= sp->bytes;
+  }
+  delete sp;
+  return LSG_OK;
+}
+
 }  // extern "C"

@@ -40,6 +40,7 @@ struct ScanDesc {
 struct KArgs {
   const ScanDesc* scans;     // device table, or null: use `one`
   const int32_t* tile_scan;  // device [ntiles] tile -> scan (batched), or null
+  const int32_t* tile_list;  // device [ntiles] local tile indices of `one`, or null: all of its tiles
   int32_t ntiles;
   int32_t nscans;
   int32_t* err;              // device error word

@@ -77,7 +77,7 @@ __device__ __forceinline__ const ScanDesc* tile_desc(const KArgs& a, int t, int&
     lt = t - d->tile0;
     return d;
   }
-  lt = t;
+  lt = a.tile_list ? a.tile_list[t] : t;
   return &a.one;
 }
 

@@ -7,9 +7,9 @@
 // capped vertical cylinders) fast enough to feed the segmentation at its own
 // rate.
 //
-// One thread per azimuth column: it culls the primitives whose azimuth
-// interval misses the column once (a bit mask over at most 256 primitives),
-// then walks the rings.  Ray directions are formed in double from the
+// One thread per azimuth column and group of 8 rings: it culls the
+// primitives whose azimuth interval misses the column once (a bit mask over
+// at most 256 primitives), then walks its rings.  Ray directions are formed in double from the
 // float32 elevation and azimuth, the intersections run in binary32.  Noise
 // and dropouts come from SplitMix64 (Steele, Lea and Flood, "Fast splittable
 // pseudorandom number generators", OOPSLA 2014) keyed by (seed, ring,
@@ -28,7 +28,7 @@ namespace {
 constexpr int PSTRIDE = 10;     // table row: kind, id, a[0..7]
 constexpr int SROW = 14;        // shared row: kind, id, a[0..7], flag, centre, lo, hi
 constexpr int NT_RAY = 128;
-constexpr int TRIG_RINGS = 1024;  // rings whose cos/sin are staged in shared memory
+constexpr int RG = 8;     // rings per thread (grid: columns x ring groups)
 constexpr float kPiF = 3.14159265358979f;
 
 __device__ __forceinline__ uint64_t smix64(uint64_t x) {
@@ -195,16 +195,15 @@ struct RayArgs {
 };
 
 __global__ void __launch_bounds__(NT_RAY) k_raycast(const __grid_constant__ RayArgs a) {
-  extern __shared__ double2 dyn[];  // [min(H, TRIG_RINGS)] (cos, sin) of the elevations, then [n][SROW] floats
-  const bool staged = a.H <= TRIG_RINGS;
+  extern __shared__ double2 dyn[];  // [RG] (cos, sin) of the group's elevations, then [n][SROW] floats
+  const int i0 = blockIdx.y * RG, i1 = min(a.H, i0 + RG);
   double2* trig = dyn;
-  float* sp = reinterpret_cast<float*>(dyn + (staged ? a.H : 0));
-  if (staged)
-    for (int i = threadIdx.x; i < a.H; i += NT_RAY) {
-      double se, ce;
-      sincos((double)a.elev[i], &se, &ce);
-      trig[i] = make_double2(ce, se);
-    }
+  float* sp = reinterpret_cast<float*>(dyn + RG);
+  for (int i = i0 + (int)threadIdx.x; i < i1; i += NT_RAY) {
+    double se, ce;
+    sincos((double)a.elev[i], &se, &ce);
+    trig[i - i0] = make_double2(ce, se);
+  }
   for (int k = threadIdx.x; k < a.n; k += NT_RAY) {
     float* row = sp + k * SROW;
     for (int q = 0; q < PSTRIDE; ++q) row[q] = (float)a.prims[(size_t)k * PSTRIDE + q];
@@ -235,15 +234,9 @@ __global__ void __launch_bounds__(NT_RAY) k_raycast(const __grid_constant__ RayA
     }
     cand[w] = m;
   }
-  for (int i = 0; i < a.H; ++i) {
-    double se, ce;
-    if (staged) {
-      const double2 t2 = trig[i];
-      ce = t2.x;
-      se = t2.y;
-    } else {
-      sincos((double)a.elev[i], &se, &ce);
-    }
+  for (int i = i0; i < i1; ++i) {
+    const double2 t2 = trig[i - i0];
+    const double ce = t2.x, se = t2.y;
     const double d0 = ce * cphi, d1 = ce * sphi, d2 = se;
     const float dx = (float)d0, dy = (float)d1, dz = (float)d2;
     float best = INFINITY;
@@ -323,9 +316,8 @@ extern "C" lsg_status lsg_raycast(const lsg_raycast_spec* spec, float* xyzr, int
   a.seed = s.seed;
   a.xyzr = xyzr;
   a.gt = gt;
-  const int grid = (s.cols + NT_RAY - 1) / NT_RAY;
-  const size_t smem = (s.rings <= TRIG_RINGS ? sizeof(double2) * (size_t)s.rings : 0) +
-                      sizeof(float) * SROW * (size_t)(s.nprims > 0 ? s.nprims : 1);
+  const dim3 grid((s.cols + NT_RAY - 1) / NT_RAY, (s.rings + RG - 1) / RG);
+  const size_t smem = sizeof(double2) * RG + sizeof(float) * SROW * (size_t)(s.nprims > 0 ? s.nprims : 1);
   k_raycast<<<grid, NT_RAY, smem, reinterpret_cast<cudaStream_t>(stream)>>>(a);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? LSG_OK : LSG_E_CUDA;

@@ -106,6 +106,11 @@ def load(build: bool = True):
             "lsg_segment_noalloc": (ctypes.c_int, [ctypes.POINTER(lsg_scan), ctypes.POINTER(lsg_params),
                                                    ctypes.POINTER(lsg_out), _P]),
             "lsg_raycast": (ctypes.c_int, [ctypes.POINTER(lsg_raycast_spec), _P, _P, _P]),
+            "lsg_spin_begin": (ctypes.c_int, [_P, ctypes.POINTER(lsg_scan), ctypes.POINTER(lsg_params),
+                                              ctypes.POINTER(lsg_out), ctypes.POINTER(_P), _P]),
+            "lsg_spin_push": (ctypes.c_int, [_P, I32, _P]),
+            "lsg_spin_finish": (ctypes.c_int, [_P, _P]),
+            "lsg_spin_destroy": (ctypes.c_int, [_P]),
             "lsg_default_params": (None, [ctypes.POINTER(lsg_params)]),
             "lsg_status_str": (ctypes.c_char_p, [ctypes.c_int]),
         }
@@ -236,6 +241,25 @@ def lsg_segment_noalloc(scan: lsg_scan, params: lsg_params, out: lsg_out, stream
     callers that may not allocate device memory.  Returns the status code."""
     return load().lsg_segment_noalloc(ctypes.byref(scan), ctypes.byref(params), ctypes.byref(out),
                                       stream or None)
+
+
+def lsg_spin_begin(ctx: int, scan: lsg_scan, params: lsg_params, out: lsg_out, stream: int = 0) -> int:
+    h = _P()
+    _check(load().lsg_spin_begin(ctx, ctypes.byref(scan), ctypes.byref(params), ctypes.byref(out),
+                                 ctypes.byref(h), stream or None), "lsg_spin_begin")
+    return h.value
+
+
+def lsg_spin_push(spin: int, cols_ready: int, stream: int = 0) -> int:
+    return load().lsg_spin_push(spin, cols_ready, stream or None)
+
+
+def lsg_spin_finish(spin: int, stream: int = 0) -> int:
+    return load().lsg_spin_finish(spin, stream or None)
+
+
+def lsg_spin_destroy(spin: int) -> None:
+    _check(load().lsg_spin_destroy(spin), "lsg_spin_destroy")
 
 
 def lsg_raycast(spec: lsg_raycast_spec, xyzr: int, gt: int, stream: int = 0) -> int:
@@ -387,6 +411,40 @@ class Context:
 
     def error(self) -> int:
         return lsg_get_error(self.h)
+
+
+class Spin:
+    """One revolution segmented while its columns arrive (lsg_spin_*): the
+    caller fills the scan's input buffer column range by column range and
+    calls push(cols_ready) after each, then finish(); the outputs equal
+    Context.segment's."""
+
+    def __init__(self, ctx: "Context", elev, xyzr=None, range_=None, az0=0.0, daz=0.0, params: "Params" = None,
+                 out: Optional["Outputs"] = None, stream=None):
+        params = params or Params()
+        src = xyzr if xyzr is not None else range_
+        H, W = int(src.shape[0]), int(src.shape[1])
+        self.out = out if out is not None else alloc_outputs(H, W, params.subsample, src.device)
+        self._keep = (make_scan(elev, xyzr, range_, az0, daz), params.to_c(), self.out.to_c())
+        self.h = lsg_spin_begin(ctx.h, *self._keep, _stream_ptr(stream))
+
+    def push(self, cols_ready: int, stream=None) -> None:
+        _check(lsg_spin_push(self.h, cols_ready, _stream_ptr(stream)), "lsg_spin_push")
+
+    def finish(self, stream=None) -> "Outputs":
+        _check(lsg_spin_finish(self.h, _stream_ptr(stream)), "lsg_spin_finish")
+        return self.out
+
+    def close(self):
+        if self.h:
+            lsg_spin_destroy(self.h)
+            self.h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class BatchPlan:

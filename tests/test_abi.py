@@ -68,3 +68,11 @@ def test_null_arguments_are_rejected_without_a_device():
     if not torch.cuda.is_available():
         assert lib.lsg_create(0, 0, ctypes.byref(h)) == lsg.LSG_E_ARG
         assert h.value is None
+
+
+def test_spin_entry_points_reject_null_handles():
+    lib = lsg.load()
+    assert lib.lsg_spin_begin(None, None, None, None, None, None) == lsg.LSG_E_ARG
+    assert lib.lsg_spin_push(None, 0, None) == lsg.LSG_E_ARG
+    assert lib.lsg_spin_finish(None, None) == lsg.LSG_E_ARG
+    assert lib.lsg_spin_destroy(None) == lsg.LSG_E_ARG
