@@ -216,7 +216,8 @@ struct Geo {
   static constexpr size_t off_tb = ((ring_bytes > lp_bytes ? ring_bytes : lp_bytes) + 15) / 16 * 16;
   static constexpr size_t off_rows = off_tb + ((NV + 15) / 16) * 16;  // long long [HR] input row offsets
   static constexpr size_t off_q = off_rows + ((sizeof(long long) * HR + 15) / 16) * 16;  // uint32 [NW][QCAP]
-  static constexpr size_t q_bytes = sizeof(uint32_t) * NW * QCAP;
+  // queue uint32 [NW][QCAP], then the run starts of every strip row uint16 [NW][TR][32]
+  static constexpr size_t q_bytes = sizeof(uint32_t) * NW * QCAP + sizeof(uint16_t) * NW * TR * 32;
   static constexpr size_t bytes = off_q + q_bytes;
   static constexpr size_t ccl_bytes = lp_bytes + ((NV + 15) / 16) * 16 + q_bytes;  // k_tile_ccl: lp, tb, queue
 };
@@ -603,8 +604,8 @@ __device__ __forceinline__ void run_starts(bool linkA, bool linkB, int lane, int
 
 template <int TR, int NW>
 __device__ __forceinline__ void tile_cross_and_roots(const Loc& L, const uint8_t* __restrict__ tb, int* lp,
-                                                     uint16_t* __restrict__ lroot, int32_t* __restrict__ parent,
-                                                     int32_t* err);
+                                                     const uint32_t* q, uint16_t* __restrict__ lroot,
+                                                     int32_t* __restrict__ parent, int32_t* err);
 
 // Tile components of the tile bytes tb[TR][TC] (mesh + homogeneity bits of
 // the tile's own vertices; zero outside the tile).  C1: each warp walks its
@@ -639,8 +640,11 @@ __device__ __forceinline__ void queue_union(uint32_t* wq, int& qn, bool f, int a
 // run's first vertex (plus the strip's and the tile's last column) enters
 // the shared-memory union-find.  A vertical edge is joined unless the
 // column to its left already joins the same two vertices (its D edge and
-// the two R edges, or its D edge and the lower R edge for a G edge); the
-// joins wait in a per-warp queue and run 32 at a time.  Then C2 / C3
+// the two R edges, or its D edge and the lower R edge for a G edge; a G
+// edge is also implied by the upper R edge and the column's own D edge:
+// every D edge is joined, by a union or through the column to its left, so
+// the implications form no cycle); the joins wait in a per-warp queue and
+// run 32 at a time.  The rows' run starts are kept for C3.  Then C2 / C3
 // (below).  Writes every vertex's tile-local root to lroot and marks each
 // root in parent.
 template <int TR, int NW>
@@ -655,6 +659,7 @@ __device__ __forceinline__ void tile_components(const Loc& L, const uint8_t* __r
   const bool act = lane >= 1 && lane <= SO / 2;
   const bool lead = lane == 0 && w > 0;        // reads the previous strip's last column
   uint32_t* wq = q + w * QCAP;
+  uint16_t* rs = reinterpret_cast<uint16_t*>(q + NW * QCAP) + w * TR * 32;  // this strip's run starts
   int qn = 0;                                  // queued unions (warp-uniform)
   uint32_t prev = 0;                           // previous row's bytes of the lane's columns
   int psA = 0, psB = 0;                        // previous row's run starts (tile-linear)
@@ -667,6 +672,7 @@ __device__ __forceinline__ void tile_components(const Loc& L, const uint8_t* __r
     const bool linkB = act && lane < SO / 2 && (bB & B_HR) && lcA + 2 < L.cn;
     int posA, posB;
     run_starts(linkA, linkB, lane, posA, posB);
+    rs[lr * 32 + lane] = (uint16_t)(posA | (posB << 8));
     const int vA = lr * TC + lcA;
     const int sA = lr * TC + base + posA, sB = lr * TC + base + posB;
     if (act) {
@@ -682,10 +688,10 @@ __device__ __forceinline__ void tile_components(const Loc& L, const uint8_t* __r
       // first column (its left: the previous lane's second column, or the
       // previous strip's last column for lane 1, whose G edge is a C2 edge)
       fDA = (pA & B_HD) && !((lpB & B_HD) && (lpB & B_HR) && (lB & B_HR));
-      fGA = lane > 1 && (lpB & B_HG) && !((lpB & B_HD) && (lB & B_HR));
+      fGA = lane > 1 && (lpB & B_HG) && !(((lpB & B_HD) && (lB & B_HR)) || ((lpB & B_HR) && (pA & B_HD)));
       // second column (its left: the first)
       fDB = (pB & B_HD) && !((pA & B_HD) && (pA & B_HR) && (bA & B_HR));
-      fGB = (pA & B_HG) && !((pA & B_HD) && (bA & B_HR));
+      fGB = (pA & B_HG) && !(((pA & B_HD) && (bA & B_HR)) || ((pA & B_HR) && (pB & B_HD)));
     }
     queue_union(wq, qn, fDA, sA, psA);
     queue_union(wq, qn, fGA, sA, upsB);
@@ -701,7 +707,7 @@ __device__ __forceinline__ void tile_components(const Loc& L, const uint8_t* __r
   }
   flush_unions(lp, wq, qn, G::NV + 1, err);
   __syncthreads();
-  tile_cross_and_roots<TR, NW>(L, tb, lp, lroot, parent, err);
+  tile_cross_and_roots<TR, NW>(L, tb, lp, q, lroot, parent, err);
 }
 
 // C2: edges across strip borders, and the seam of a tile spanning the ring
@@ -711,8 +717,8 @@ __device__ __forceinline__ void tile_components(const Loc& L, const uint8_t* __r
 // vertex, roots marked in the global union-find.
 template <int TR, int NW>
 __device__ __forceinline__ void tile_cross_and_roots(const Loc& L, const uint8_t* __restrict__ tb, int* lp,
-                                                     uint16_t* __restrict__ lroot, int32_t* __restrict__ parent,
-                                                     int32_t* err) {
+                                                     const uint32_t* q, uint16_t* __restrict__ lroot,
+                                                     int32_t* __restrict__ parent, int32_t* err) {
   using G = Geo<TR, NW>;
   constexpr int TC = G::TC;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -740,13 +746,12 @@ __device__ __forceinline__ void tile_cross_and_roots(const Loc& L, const uint8_t
   const int lcA = w * SO + 2 * lane - 2;
   const bool act = lane >= 1 && lane <= SO / 2;
   const size_t pitch = root_pitch(L.Ws);
+  const uint16_t* rs = reinterpret_cast<const uint16_t*>(q + NW * QCAP) + w * TR * 32;  // C1's run starts
   for (int lr = 0; lr < L.rn; ++lr) {
     const uint32_t cur = act ? *reinterpret_cast<const uint16_t*>(tb + lr * TC + lcA) : 0u;
     const uint32_t bA = cur & 0xffu, bB = cur >> 8;
-    const bool linkA = act && (bA & B_HR) && lcA + 1 < L.cn;
-    const bool linkB = act && lane < SO / 2 && (bB & B_HR) && lcA + 2 < L.cn;
-    int posA, posB;
-    run_starts(linkA, linkB, lane, posA, posB);
+    const uint32_t ps = rs[lr * 32 + lane];
+    const int posA = (int)(ps & 0xffu), posB = (int)(ps >> 8);
     const int vA = lr * TC + lcA;
     int rA = 0, rB = 0;
     if (act && posA == 2 * lane) rA = find_sh(lp, vA, G::NV + 1);
