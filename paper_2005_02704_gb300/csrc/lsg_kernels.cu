@@ -305,10 +305,13 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return y;
 }
 
-// Lengths of two vectors: q * rsqrt(q), exact 0 for a zero vector.
+// Lengths of two vectors: q * rsqrt(q) + 1e-30 (the offset leaves every
+// length above 1e-23 unchanged and keeps a sum of two lengths nonzero, so
+// the reciprocal weights below stay finite).
 __device__ __forceinline__ float2 len2(float2 x, float2 y, float2 z) {
   const float2 q = fma2(x, x, fma2(y, y, mul2(z, z)));
-  return mul2(q, make_float2(rsq_approx(fmaxf(q.x, FLT_MIN)), rsq_approx(fmaxf(q.y, FLT_MIN))));
+  return fma2(q, make_float2(rsq_approx(fmaxf(q.x, FLT_MIN)), rsq_approx(fmaxf(q.y, FLT_MIN))),
+              make_float2(1e-30f, 1e-30f));
 }
 
 // Depth-jump cut of two edges: |r_p - r_q| > tau * min(r_p, r_q) in
@@ -321,13 +324,13 @@ __device__ __forceinline__ void jump_cut2(float2 rp, float2 rq, float2 tau, bool
 }
 
 // One weighted triangle term of two vertices' normal sums (Sec. 2, normal
-// estimation): w (a x b) with w = 1 / (|a| + |b|), added only where the
-// triangle exists.  Points out of range have zero coordinates, so every
-// spoke is finite and a missing triangle's term is removed by a zero weight.
+// estimation): w (a x b) with w = 1 / (|a| + |b|), times the triangle's
+// existence (exactly 0 or 1).  Points out of range have zero coordinates, so
+// every spoke is finite and a missing triangle's term is an exact zero.
 __device__ __forceinline__ void tri2(float2 ax, float2 ay, float2 az, float2 la, float2 bx, float2 by, float2 bz,
-                                     float2 lb, bool ta, bool tb, float2& sx, float2& sy, float2& sz) {
+                                     float2 lb, float2 ex, float2& sx, float2& sy, float2& sz) {
   const float2 l = add2(la, lb);
-  const float2 wt = make_float2(ta ? rcp_approx(l.x) : 0.f, tb ? rcp_approx(l.y) : 0.f);
+  const float2 wt = mul2(make_float2(rcp_approx(l.x), rcp_approx(l.y)), ex);
   const float2 cx = fma2(ay, bz, mul2(neg2(az), by));
   const float2 cy = fma2(az, bx, mul2(neg2(ax), bz));
   const float2 cz = fma2(ax, by, mul2(neg2(ay), bx));
@@ -435,6 +438,7 @@ __device__ __forceinline__ void tile_sweep(const ScanDesc* d, const Loc& L, unsi
   const float QNAN = __int_as_float(0x7fc00000);
   float2 ppx = Z2, ppy = Z2, ppz = Z2, ppr = make_float2(-1.f, -1.f);  // row k-1 (zeroed out of range)
   float2 rx1 = Z2, ry1 = Z2, rz1 = Z2, lr1 = Z2;                        // R edges of row k-1
+  float2 er1 = Z2;                                                      // their existence (0 / 1)
   float2 ux = Z2, uy = Z2, uz = Z2;                // row k-1's normal sums: the terms above it
   float2 nx2 = make_float2(QNAN, QNAN), ny2 = nx2, nz2 = nx2;  // normals of row k-2 (NaN: none)
   uint32_t m2 = 0;   // mesh bytes of row k-2 (first | second << 8)
@@ -476,22 +480,24 @@ __device__ __forceinline__ void tile_sweep(const ScanDesc* d, const Loc& L, unsi
     const bool GA = vpA && vB && !gA, GB = vpB && vN && !gB;
     win |= ((DA ? B_D : 0u) | (GA ? B_G : 0u)) | (((DB ? B_D : 0u) | (GB ? B_G : 0u)) << 8) |
            ((((RA ? B_R : 0u) | (vA ? B_VALID : 0u)) | (((RB ? B_R : 0u) | (vB ? B_VALID : 0u)) << 8)) << 16);
-    const uint32_t up = __shfl_up_sync(FULL, win, 1), dn = __shfl_down_sync(FULL, win, 1);
-    // the left neighbour's bytes (row k-1, row k) and the right neighbour's (row k-1)
+    // triangle existence as exact 0 / 1 products: the lower (d, g, r) and
+    // upper (g, r above, d to the right) triangles of each column's quad
+    // between rows k-1 and k, and the same two of the quad to its left
+    const float2 eD = make_float2(DA ? 1.f : 0.f, DB ? 1.f : 0.f);
+    const float2 eG = make_float2(GA ? 1.f : 0.f, GB ? 1.f : 0.f);
+    const float2 eR = make_float2(RA ? 1.f : 0.f, RB ? 1.f : 0.f);
+    const float2 tLo = mul2(mul2(eD, eG), eR);
+    const float2 tUp = mul2(mul2(eG, er1), right_of(eD));
+    const float2 tLoL = left_of(tLo), tUpL = left_of(tUp);
     const uint32_t m1A = win & 0xffu, m1B = (win >> 8) & 0xffu;
-    const uint32_t l1A = up >> 8 & 0xffu, l0A = up >> 24;  // left of the first column: previous lane's second
-    const uint32_t l1B = m1A;                              // left of the second: the first
-    const uint32_t r1B = dn & 0xffu;                       // right of the second: next lane's first
     // R edges of row k-1 ending at each column (below: F of row k-1)
     const float2 fx1 = left_of(rx1), fy1 = left_of(ry1), fz1 = left_of(rz1), lf1 = left_of(lr1);
 
     // normals of row k-1: the three terms below it
     float2 sx = ux, sy = uy, sz = uz;
-    tri2(dx, dy, dz, ld, gx, gy, gz, lg, DA && GA && RA, DB && GB && RB, sx, sy, sz);
-    tri2(gx, gy, gz, lg, rx1, ry1, rz1, lr1, GA && (m1A & B_R) && DB, GB && (m1B & B_R) && (r1B & B_D), sx, sy,
-         sz);
-    tri2(dx, dy, dz, ld, fx1, fy1, fz1, lf1, (l1A & B_R) && DA && (l1A & B_G), (l1B & B_R) && DB && (l1B & B_G),
-         sx, sy, sz);
+    tri2(dx, dy, dz, ld, gx, gy, gz, lg, tLo, sx, sy, sz);
+    tri2(gx, gy, gz, lg, rx1, ry1, rz1, lr1, tUp, sx, sy, sz);
+    tri2(dx, dy, dz, ld, fx1, fy1, fz1, lf1, tUpL, sx, sy, sz);
     const float2 q2 = fma2(sx, sx, fma2(sy, sy, mul2(sz, sz)));
     // a sum shorter than 2^-63 counts as no normal (as does a zero sum)
     const bool hA = (m1A & B_VALID) && q2.x >= FLT_MIN && q2.x < 3.0e38f;
@@ -505,15 +511,12 @@ __device__ __forceinline__ void tile_sweep(const ScanDesc* d, const Loc& L, unsi
     {
       const float2 fx = left_of(ex), fy = left_of(ey), fz = left_of(ez), lf = left_of(le);
       const float2 glx = left_of(gx), gly = left_of(gy), glz = left_of(gz), lgl = left_of(lg);
-      const bool DlA = l1A & B_D, DlB = DA;  // D edge of the left column, row k-1
-      const bool GlA = l1A & B_G, GlB = GA;  // G edge of the left column, row k-1
-      const bool RlA = l0A & B_R, RlB = RA;  // R edge of the left column, row k
       ux = Z2;
       uy = Z2;
       uz = Z2;
-      tri2(dx, dy, dz, ld, ex, ey, ez, le, RA && DA && GA, RB && DB && GB, ux, uy, uz);
-      tri2(dx, dy, dz, ld, glx, gly, glz, lgl, DA && GlA && (l1A & B_R), DB && GlB && (l1B & B_R), ux, uy, uz);
-      tri2(glx, gly, glz, lgl, fx, fy, fz, lf, GlA && RlA && DlA, GlB && RlB && DlB, ux, uy, uz);
+      tri2(dx, dy, dz, ld, ex, ey, ez, le, tLo, ux, uy, uz);
+      tri2(dx, dy, dz, ld, glx, gly, glz, lgl, tUpL, ux, uy, uz);
+      tri2(glx, gly, glz, lgl, fx, fy, fz, lf, tLoL, ux, uy, uz);
     }
 
     // homogeneity mask and outputs of row k-2
@@ -578,6 +581,7 @@ __device__ __forceinline__ void tile_sweep(const ScanDesc* d, const Loc& L, unsi
     ry1 = ey;
     rz1 = ez;
     lr1 = le;
+    er1 = eR;
     nx2 = nx1;
     ny2 = ny1;
     nz2 = nz1;
