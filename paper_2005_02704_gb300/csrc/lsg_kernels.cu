@@ -305,13 +305,14 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return y;
 }
 
-// Lengths of two vectors: q * rsqrt(q) + 1e-30 (the offset leaves every
-// length above 1e-23 unchanged and keeps a sum of two lengths nonzero, so
-// the reciprocal weights below stay finite).
+// Lengths of two vectors: q * rsqrt(q + 1e-37) + 1e-30.  The offsets leave
+// every length above 1e-23 unchanged, keep the reciprocal square root finite
+// for a zero vector (whose length comes out as 1e-30) and keep a sum of two
+// lengths nonzero, so the reciprocal weights below stay finite.
 __device__ __forceinline__ float2 len2(float2 x, float2 y, float2 z) {
   const float2 q = fma2(x, x, fma2(y, y, mul2(z, z)));
-  return fma2(q, make_float2(rsq_approx(fmaxf(q.x, FLT_MIN)), rsq_approx(fmaxf(q.y, FLT_MIN))),
-              make_float2(1e-30f, 1e-30f));
+  const float2 qg = add2(q, make_float2(1e-37f, 1e-37f));
+  return fma2(q, make_float2(rsq_approx(qg.x), rsq_approx(qg.y)), make_float2(1e-30f, 1e-30f));
 }
 
 // Depth-jump cut of two edges: |r_p - r_q| > tau * min(r_p, r_q) in
@@ -489,7 +490,6 @@ __device__ __forceinline__ void tile_sweep(const ScanDesc* d, const Loc& L, unsi
     const float2 tLo = mul2(mul2(eD, eG), eR);
     const float2 tUp = mul2(mul2(eG, er1), right_of(eD));
     const float2 tLoL = left_of(tLo), tUpL = left_of(tUp);
-    const uint32_t m1A = win & 0xffu, m1B = (win >> 8) & 0xffu;
     // R edges of row k-1 ending at each column (below: F of row k-1)
     const float2 fx1 = left_of(rx1), fy1 = left_of(ry1), fz1 = left_of(rz1), lf1 = left_of(lr1);
 
@@ -499,9 +499,10 @@ __device__ __forceinline__ void tile_sweep(const ScanDesc* d, const Loc& L, unsi
     tri2(gx, gy, gz, lg, rx1, ry1, rz1, lr1, tUp, sx, sy, sz);
     tri2(dx, dy, dz, ld, fx1, fy1, fz1, lf1, tUpL, sx, sy, sz);
     const float2 q2 = fma2(sx, sx, fma2(sy, sy, mul2(sz, sz)));
-    // a sum shorter than 2^-63 counts as no normal (as does a zero sum)
-    const bool hA = (m1A & B_VALID) && q2.x >= FLT_MIN && q2.x < 3.0e38f;
-    const bool hB = (m1B & B_VALID) && q2.y >= FLT_MIN && q2.y < 3.0e38f;
+    // a sum shorter than 2^-63 counts as no normal (as does a zero sum, which
+    // is what a vertex out of range has: none of its triangles exists)
+    const bool hA = q2.x >= FLT_MIN && q2.x < 3.0e38f;
+    const bool hB = q2.y >= FLT_MIN && q2.y < 3.0e38f;
     const float nsign = d->nsign;
     const float2 fn = make_float2(hA ? nsign * rsq_approx(q2.x) : QNAN, hB ? nsign * rsq_approx(q2.y) : QNAN);
     const float2 nx1 = mul2(sx, fn), ny1 = mul2(sy, fn), nz1 = mul2(sz, fn);
