@@ -68,6 +68,7 @@ def parse():
     ap.add_argument("--no-spin", action="store_true", help="skip the streaming (per-packet) latency measurement")
     ap.add_argument("--phased", action="store_true", help="force four phased launches (else the autotuner's choice)")
     ap.add_argument("--fused", action="store_true", help="force the single persistent launch")
+    ap.add_argument("--grouped", action="store_true", help="force the grouped schedule")
     ap.add_argument("--e2e-chunks", type=int, default=16, help="chunks of the pipelined end-to-end path")
     ap.add_argument("--tile", default=None, help="force a tile shape (e.g. 32x240) instead of autotuning")
     ap.add_argument("--serve-scale", type=float, default=10.0,
@@ -147,6 +148,10 @@ def measured_hbm():
             return float(json.load(f)["hbm_gbs"]), "measured"
     except Exception:
         return FALLBACK_HBM_GBS, "fallback"
+
+
+SCHEDULES = {0: "phased (4 launches)", 1: "fused (one persistent launch)",
+             2: "grouped (ring order, then 4 scan groups of tile / merge / label launches on parallel graph branches)"}
 
 
 def profiled_traffic(kernel: str):
@@ -405,9 +410,12 @@ def main():
     if not args.no_autotune and not args.tile:
         tuned = plan.autotune(reps=3)
     if args.phased:
-        plan.set_fused(False)
+        plan.set_schedule(0)
     if args.fused:
-        plan.set_fused(True)
+        plan.set_schedule(1)
+    if args.grouped:
+        plan.set_schedule(2)
+    schedule = plan.schedule
     tile_name = {v: k for k, v in lsg.TILES.items()}[plan.tile]
 
     # ---- batched path, inputs resident ------------------------------------
@@ -434,19 +442,25 @@ def main():
     value = pts_all / (ms_step / 1e3)
 
     # ---- per-phase device times (events recorded inside the graph) ---------
+    # (the grouped schedule overlaps its kernels, so its per-kernel times are
+    # taken from the phased capture of the same plan)
     phase = [0.0, 0.0, 0.0, 0.0]
     nrep = max(3, min(args.steps, 10))
+    if schedule == 2:
+        plan.set_schedule(0)
     for _ in range(nrep):
         plan.run()
         t = plan.phase_times()
         phase = [a + b for a, b in zip(phase, t)]
     phase = [x / nrep for x in phase]
+    if schedule == 2:
+        plan.set_schedule(2)
 
     # ---- end to end through the C ABI with host buffers --------------------
     # (a) the pipelined host path: chunks of scans whose copies in both
     #     directions overlap the other chunks' passes; (b) for reference, the
     #     same copies and the single-plan pass queued one after the other
-    pipe = db.pipeline(ctx, plan.tile, chunks=args.e2e_chunks, fused=plan.fused)
+    pipe = db.pipeline(ctx, plan.tile, chunks=args.e2e_chunks, schedule=schedule)
     for _ in range(max(args.warmup, 3)):
         pipe.step(stream)
     torch.cuda.synchronize()
@@ -525,7 +539,7 @@ def main():
     # kernel is the tile kernel
     peak, peak_kind = measured_hbm()
     t_dom = phase[1] / 1e3
-    fused = plan.fused
+    fused = schedule == 1
     bpp = PATH_BYTES_PER_POINT if fused else TILE_BYTES_PER_POINT
     achieved = bpp * db.points / t_dom / 1e9
     traffic_pp = profiled_traffic("k_fused" if fused else "k_tile")
@@ -555,7 +569,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "scans_per_gpu": db.n, "points_per_gpu": db.points,
-                       "tile": tile_name, "schedule": "fused (one persistent launch)" if fused else "phased (4 launches)",
+                       "tile": tile_name, "schedule": SCHEDULES[schedule],
                        "autotune_ms": tuned[1] if tuned else None,
                        "l2": "inputs larger than L2 (x,y,z,r %.2f GB per GPU > 129 MB), no flush" % (
                            db.points * 16 / 1e9),

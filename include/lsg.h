@@ -263,8 +263,8 @@ lsg_status lsg_reserve(lsg_ctx* ctx, size_t workspace_bytes, int32_t max_scans, 
 /* Replays the plan's graph on `stream`. */
 lsg_status lsg_batch_run(lsg_plan* plan, lsg_stream stream);
 
-/* Times every tile shape under both schedules (fused and phased, see
- * lsg_plan_set_fused) on the plan (reps replays each, CUDA events on
+/* Times every tile shape under the three schedules (see lsg_plan_set_fused)
+ * on the plan (reps replays each, CUDA events on
  * `stream`), keeps the fastest and re-captures the graph.  *best_tile and
  * *best_ms (either may be NULL) receive the choice and its time per pass;
  * lsg_plan_fused tells the schedule chosen. */
@@ -273,23 +273,30 @@ lsg_status lsg_autotune(lsg_plan* plan, int reps, lsg_stream stream, int* best_t
 /* Tile shape the plan currently uses. */
 int lsg_plan_tile(const lsg_plan* plan);
 
-/* Chooses how the plan's pass runs: fused = 1 (the default) is one
- * persistent launch that walks a schedule of work items (each scan's ring
- * order, then per tile: geometry and tile components, border merge, labels),
- * each item waiting (bounded) only on items scheduled before it; fused = 0 is
- * four phased launches (ring order, tiles, merges, labels).  Outputs are
- * identical.  Re-captures the graph. */
+/* Chooses how the plan's pass runs (the schedule):
+ *   1 (the default) one persistent launch that walks a list of work items
+ *     (each scan's ring order, then per tile: geometry and tile components,
+ *     border merge, labels), each item waiting (bounded) only on items
+ *     listed before it;
+ *   0 four phased launches (ring order, tiles, merges, labels);
+ *   2 the ring order, then the scans in four groups of about equal tile
+ *     counts, each group's tile, merge and label launches on its own branch
+ *     of the graph, so a group's merges and labels overlap the tile work of
+ *     the groups still running.
+ * Any other value means 0.  Outputs are identical.  Re-captures the graph. */
 lsg_status lsg_plan_set_fused(lsg_plan* plan, int fused);
 
-/* 1 when the plan runs fused, 0 when phased. */
+/* The plan's schedule (0, 1 or 2, see lsg_plan_set_fused). */
 int lsg_plan_fused(const lsg_plan* plan);
 
 /* Device time of each phase of the plan's last replay, in milliseconds.
  * Phased plans: ms[0] ring order, ms[1] tile kernel (decode, mesh, normals,
  * edge mask, tile-local components), ms[2] border merge, ms[3] labels and
  * back-fill.  Fused plans: ms[0] counter reset, ms[1] the persistent launch
- * (the whole pass), ms[2] = ms[3] = 0.  Measured by CUDA events recorded
- * inside the graph; waits for the replay to finish. */
+ * (the whole pass), ms[2] = ms[3] = 0.  Grouped plans (schedule 2): ms[0] ring
+ * order, ms[1] the grouped branches (the rest of the pass), ms[2] = ms[3] =
+ * 0.  Measured by CUDA events recorded inside the graph; waits for the
+ * replay to finish. */
 lsg_status lsg_plan_phase_times(lsg_plan* plan, float* ms);
 
 /* Frees the plan (synchronises the device first). */

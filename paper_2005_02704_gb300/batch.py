@@ -134,8 +134,8 @@ class DeviceBatch:
         return lsg.BatchPlan(ctx, self.c_scans(), self.c_params(), self.c_outs(), tile)
 
     def pipeline(self, ctx: "lsg.Context", tile: int = lsg.LSG_TILE_AUTO, chunks: int = 8,
-                 fused=None) -> "HostPipeline":
-        return HostPipeline(self, ctx, tile, chunks, fused)
+                 schedule=None) -> "HostPipeline":
+        return HostPipeline(self, ctx, tile, chunks, schedule)
 
     # ---- per-scan views of the device outputs -----------------------------
     def view(self, b: int):
@@ -166,7 +166,7 @@ class HostPipeline:
     """
 
     def __init__(self, db: DeviceBatch, ctx: "lsg.Context", tile: int = lsg.LSG_TILE_AUTO, chunks: int = 8,
-                 fused=None):
+                 schedule=None):
         torch = db.torch
         self.db = db
         n = db.n
@@ -180,9 +180,9 @@ class HostPipeline:
         self.ranges = [(b0, b1) for b0, b1 in zip(bounds[:-1], bounds[1:]) if b1 > b0]
         scans, params, outs = db.c_scans(), db.c_params(), db.c_outs()
         self.plans = [lsg.BatchPlan(ctx, scans[b0:b1], params[b0:b1], outs[b0:b1], tile) for b0, b1 in self.ranges]
-        if fused is not None:
+        if schedule is not None:
             for p in self.plans:
-                p.set_fused(bool(fused))
+                p.set_schedule(int(schedule))
         self.s_in = torch.cuda.Stream(db.dev)
         self.s_run = torch.cuda.Stream(db.dev)
         self.s_out = torch.cuda.Stream(db.dev)

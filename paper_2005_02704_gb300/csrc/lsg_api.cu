@@ -566,6 +566,9 @@ static lsg_status plan_layout(lsg_plan* pl, int tile) {
   return cuda_status(e);
 }
 
+// Scan groups of the overlapped schedule.
+constexpr int kGroups = 4;
+
 static lsg_status plan_capture(lsg_plan* pl) {
   if (pl->exec) cudaGraphExecDestroy(pl->exec);
   if (pl->graph) cudaGraphDestroy(pl->graph);
@@ -583,6 +586,17 @@ static lsg_status plan_capture(lsg_plan* pl) {
   a.err = pl->ctx->d_err;
   for (int k = 0; k < 5 && e == cudaSuccess; ++k)
     if (!pl->ev[k]) e = cudaEventCreate(&pl->ev[k]);
+  // side streams and fork / join events of the grouped schedule
+  cudaStream_t side[kGroups] = {};
+  cudaEvent_t fork[kGroups] = {}, join[kGroups] = {};
+  bool joined[kGroups] = {};
+  if (pl->fused == 2) {
+    for (int g = 0; g < kGroups && e == cudaSuccess; ++g) {
+      e = cudaStreamCreateWithFlags(&side[g], cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork[g], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join[g], cudaEventDisableTiming);
+    }
+  }
   if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   lsg_status st = LSG_OK;
   if (e == cudaSuccess) {
@@ -590,7 +604,41 @@ static lsg_status plan_capture(lsg_plan* pl) {
     // runs one block per scan); the tile kernels see only non-empty scans.
     // Event-record nodes between the phases give per-kernel device times.
     cudaError_t le = cudaEventRecordWithFlags(pl->ev[0], cs, cudaEventRecordExternal);
-    if (pl->fused) {
+    if (pl->fused == 2) {
+      // scan groups of about equal tile counts, each a chain of the tile,
+      // merge and label kernels on its own branch of the graph: as one
+      // group's tiles finish, its latency-bound merge and labels run beside
+      // the other groups' tile work
+      if (le == cudaSuccess) le = launch_prep(a, cs);
+      if (le == cudaSuccess) le = cudaEventRecordWithFlags(pl->ev[1], cs, cudaEventRecordExternal);
+      if (le == cudaSuccess) le = cudaEventRecord(fork[0], cs);
+      int b0 = 0;
+      for (int g = 0; g < kGroups && le == cudaSuccess; ++g) {
+        const int32_t t0 = pl->host_desc[b0].tile0;
+        const int32_t target = (int32_t)(((int64_t)pl->ntiles * (g + 1)) / kGroups);
+        int b1 = b0;
+        while (b1 < pl->n && (pl->host_desc[b1].tile0 < target || b1 == b0)) ++b1;
+        if (g == kGroups - 1) b1 = pl->n;
+        const int32_t t1 = b1 < pl->n ? pl->host_desc[b1].tile0 : pl->ntiles;
+        b0 = b1;
+        if (t1 <= t0) continue;
+        KArgs ag = a;
+        ag.tile_base = t0;
+        ag.ntiles = t1 - t0;
+        joined[g] = true;
+        le = cudaStreamWaitEvent(side[g], fork[0], 0);
+        if (le == cudaSuccess) le = launch_tile(pl->tile, ag, side[g]);
+        if (le == cudaSuccess) le = launch_merge(pl->tile, ag, side[g]);
+        if (le == cudaSuccess) le = launch_flatten(pl->tile, ag, side[g]);
+        if (le == cudaSuccess) le = cudaEventRecord(join[g], side[g]);
+        if (b0 >= pl->n) break;
+      }
+      for (int g = 0; g < kGroups && le == cudaSuccess; ++g)
+        if (joined[g]) le = cudaStreamWaitEvent(cs, join[g], 0);
+      if (le == cudaSuccess) le = cudaEventRecordWithFlags(pl->ev[2], cs, cudaEventRecordExternal);
+      if (le == cudaSuccess) le = cudaEventRecordWithFlags(pl->ev[3], cs, cudaEventRecordExternal);
+      if (le == cudaSuccess) le = cudaEventRecordWithFlags(pl->ev[4], cs, cudaEventRecordExternal);
+    } else if (pl->fused) {
       // counters reset, then the single persistent launch
       FusedArgs f;
       f.scans = pl->d_desc;
@@ -620,6 +668,11 @@ static lsg_status plan_capture(lsg_plan* pl) {
   }
   if (e == cudaSuccess) e = cudaGraphInstantiate(&pl->exec, pl->graph, 0);
   st = cuda_status(e);
+  for (int g = 0; g < kGroups; ++g) {
+    if (side[g]) cudaStreamDestroy(side[g]);
+    if (fork[g]) cudaEventDestroy(fork[g]);
+    if (join[g]) cudaEventDestroy(join[g]);
+  }
   cudaStreamDestroy(cs);
   return st;
 }
@@ -688,7 +741,7 @@ int lsg_plan_tile(const lsg_plan* plan) { return plan ? plan->tile : -1; }
 lsg_status lsg_plan_set_fused(lsg_plan* plan, int fused) {
   if (!plan) return LSG_E_ARG;
   DeviceGuard g(plan->ctx->device);
-  plan->fused = fused ? 1 : 0;
+  plan->fused = (fused == 1 || fused == 2) ? fused : 0;
   return plan_capture(plan);
 }
 
@@ -713,8 +766,9 @@ lsg_status lsg_autotune(lsg_plan* plan, int reps, lsg_stream stream, int* best_t
   int best = plan->tile, best_fused = plan->fused;
   float best_t = INFINITY;
   lsg_status st = LSG_OK;
-  // every tile shape under both schedules (one persistent launch, or four)
-  for (int fused = 1; fused >= 0 && st == LSG_OK; --fused) {
+  // every tile shape under every schedule (one persistent launch, four
+  // launches, scan groups on overlapping branches)
+  for (int fused = 2; fused >= 0 && st == LSG_OK; --fused) {
     for (int t = 0; t < LSG_TILE_COUNT && st == LSG_OK; ++t) {
       plan->fused = fused;
       st = plan_layout(plan, t);

@@ -42,6 +42,7 @@ struct KArgs {
   const int32_t* tile_scan;  // device [ntiles] tile -> scan (batched), or null
   const int32_t* tile_list;  // device [ntiles] local tile indices of `one`, or null: all of its tiles
   int32_t ntiles;
+  int32_t tile_base;         // batched: first entry of tile_scan this launch covers
   int32_t nscans;
   int32_t* err;              // device error word
   ScanDesc one;

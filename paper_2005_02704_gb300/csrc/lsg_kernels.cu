@@ -73,8 +73,9 @@ __device__ __forceinline__ bool in_range(float r, float rmin, float rmax) {
 
 __device__ __forceinline__ const ScanDesc* tile_desc(const KArgs& a, int t, int& lt) {
   if (a.scans) {
-    const ScanDesc* d = a.scans + a.tile_scan[t];
-    lt = t - d->tile0;
+    const int tg = t + a.tile_base;
+    const ScanDesc* d = a.scans + a.tile_scan[tg];
+    lt = tg - d->tile0;
     return d;
   }
   lt = a.tile_list ? a.tile_list[t] : t;

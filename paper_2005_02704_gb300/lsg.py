@@ -215,8 +215,9 @@ def lsg_plan_tile(plan: int) -> int:
     return load().lsg_plan_tile(plan)
 
 
-def lsg_plan_set_fused(plan: int, fused: bool) -> None:
-    _check(load().lsg_plan_set_fused(plan, 1 if fused else 0), "lsg_plan_set_fused")
+def lsg_plan_set_fused(plan: int, schedule: int) -> None:
+    """0 phased, 1 one persistent launch, 2 scan groups on overlapping branches."""
+    _check(load().lsg_plan_set_fused(plan, int(schedule)), "lsg_plan_set_fused")
 
 
 def lsg_plan_phase_times(plan: int):
@@ -467,7 +468,15 @@ class BatchPlan:
         return lsg_plan_tile(self.h)
 
     def set_fused(self, fused: bool):
-        lsg_plan_set_fused(self.h, fused)
+        lsg_plan_set_fused(self.h, 1 if fused else 0)
+
+    def set_schedule(self, schedule: int):
+        """0 phased, 1 one persistent launch, 2 scan groups on overlapping branches."""
+        lsg_plan_set_fused(self.h, int(schedule))
+
+    @property
+    def schedule(self) -> int:
+        return load().lsg_plan_fused(self.h)
 
     @property
     def fused(self) -> bool:

@@ -55,15 +55,16 @@ def mixed_specs(n, seed0):
     return specs
 
 
-@pytest.mark.parametrize("fused", [True, False], ids=["fused", "phased"])
+@pytest.mark.parametrize("schedule", [1, 0, 2], ids=["fused", "phased", "grouped"])
 @pytest.mark.parametrize("tile", ["16x240", "32x120", "32x240", "32x480", "64x240"])
-def test_batch_equals_per_scan(ctx, tile, fused):
+def test_batch_equals_per_scan(ctx, tile, schedule):
     lsg, _ = mods()
     specs = mixed_specs(12, 5000)
     scans = [lidarsim.make_scan(sp) for sp in specs]
     db = make_batch(specs, scans)
     plan = db.plan(ctx, lsg.TILES[tile])
-    plan.set_fused(fused)
+    plan.set_schedule(schedule)
+    assert plan.schedule == schedule
     plan.run()
     plan.run()  # replays are idempotent
     torch.cuda.synchronize()
@@ -149,7 +150,9 @@ def test_host_pipeline_equals_plan(ctx, chunks):
     want_lab, want_nseg = db.d_lab.cpu().clone(), db.d_nseg.cpu().clone()
     db.d_lab.fill_(-7)
     db.d_nseg.fill_(-7)
-    pipe = db.pipeline(ctx, lsg.TILES["32x120"], chunks=chunks, fused=False)
+    # chunk plans of one or two scans under the grouped schedule cover
+    # plans with fewer scans than groups
+    pipe = db.pipeline(ctx, lsg.TILES["32x120"], chunks=chunks, schedule=2 if chunks == 8 else 0)
     assert len(pipe.ranges) == min(chunks, db.n)
     assert pipe.ranges[0][0] == 0 and pipe.ranges[-1][1] == db.n
     h2d, d2h = pipe.step()
