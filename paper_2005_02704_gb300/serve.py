@@ -19,7 +19,9 @@ without a GPU.
 from __future__ import annotations
 
 import collections
+import contextlib
 import ctypes
+import gc
 import math
 import time
 from dataclasses import dataclass, field
@@ -301,10 +303,34 @@ def _request(feed: SensorFeed, ticket: int, t_arrival: float, keep_geometry: boo
                    keep_geometry=keep_geometry, c_params=feed.c_params)
 
 
+@contextlib.contextmanager
+def no_gc_pauses():
+    """Pauses Python's cyclic garbage collector (after moving the objects that
+    exist now out of its reach) for a latency-sensitive host loop: a full
+    collection over a large heap stalls the loop for milliseconds.  The loop
+    creates no reference cycles, so nothing is left for the collector."""
+    was = gc.isenabled()
+    gc.collect()
+    gc.freeze()
+    gc.disable()
+    try:
+        yield
+    finally:
+        if was:
+            gc.enable()
+        gc.unfreeze()
+
+
 def run_served(server: Server, feeds: Sequence[SensorFeed], trace, time_scale: float,
                keep_geometry: bool = False) -> dict:
     """Replays the trace (virtual seconds / time_scale = wall seconds) through
     the server; returns latency and throughput statistics."""
+    with no_gc_pauses():
+        return _run_served(server, feeds, trace, time_scale, keep_geometry)
+
+
+def _run_served(server: Server, feeds: Sequence[SensorFeed], trace, time_scale: float,
+                keep_geometry: bool) -> dict:
     t0 = time.perf_counter()
     i = 0
     reqs = []
@@ -324,6 +350,11 @@ def run_served(server: Server, feeds: Sequence[SensorFeed], trace, time_scale: f
 def run_serial(feeds: Sequence[SensorFeed], trace, time_scale: float, device: int = 0) -> dict:
     """The plain per-scan loop: one scan at a time in arrival order (upload,
     lsg_segment, download, synchronise), on one stream."""
+    with no_gc_pauses():
+        return _run_serial(feeds, trace, time_scale, device)
+
+
+def _run_serial(feeds: Sequence[SensorFeed], trace, time_scale: float, device: int) -> dict:
     import torch
     dev = torch.device("cuda", device)
     ctx = lsg.Context(device)
