@@ -83,10 +83,10 @@ __device__ __forceinline__ const ScanDesc* tile_desc(const KArgs& a, int t, int&
 }
 
 // Union-find on shared memory.  P[x] <= x always holds, so the forest has no
-// cycles and the root of every tree is its smallest index.
-// find with path halving on shared memory: each visited node is re-pointed
-// at its grandparent.  The store only shortens a path to an ancestor
-// (P[x] <= x still holds), so it is safe next to concurrent atomicMin links.
+// cycles and the root of every tree is its smallest index.  find with path
+// halving: each visited node is re-pointed at its grandparent; the store
+// only shortens a path to an ancestor (P[x] <= x still holds), so it is safe
+// next to concurrent atomicMin links.
 __device__ __forceinline__ int find_sh(int* P, int x, int limit) {
   volatile int* V = P;
   int p = V[x];
@@ -117,19 +117,7 @@ __device__ void union_sh(int* P, int a, int b, int limit, int32_t* err) {
 }
 
 // Union-find on global memory: loads bypass L1 (ld.global.cg) so they see the
-// atomics, which resolve in L2.
-__device__ __forceinline__ int find_g(const int32_t* P, int x, int limit) {
-  int p = __ldcg(P + x);
-  while (p != x && limit-- > 0) {
-    x = p;
-    p = __ldcg(P + x);
-  }
-  return x;
-}
-
-// find with path halving: each visited node is re-pointed at its grandparent.
-// The store only shortens a path to an ancestor (P[x] <= x still holds), so it
-// is safe next to concurrent atomicMin links.
+// atomics, which resolve in L2.  find with path halving, as above.
 __device__ __forceinline__ int find_halve(int32_t* P, int x, int limit) {
   int p = __ldcg(P + x);
   while (p != x && limit-- > 0) {
@@ -168,6 +156,10 @@ constexpr int NT_PREP = 256;
 template <int NTB>
 __device__ __forceinline__ void prep_body(const ScanDesc* d, float* se, int32_t* err) {
   const int H = d->H;
+  if (H == 0 || d->W == 0) {  // no points: nothing but the count (elevations unread)
+    if (threadIdx.x == 0) *d->nseg = 0;
+    return;
+  }
   for (int k = threadIdx.x; k < H; k += NTB) {
     se[k] = d->elev[k];
     d->order[k] = -1;

@@ -162,3 +162,40 @@ def test_host_pipeline_equals_plan(ctx, chunks):
     assert torch.equal(db.h_lab, want_lab) and torch.equal(db.h_nseg, want_nseg)
     pipe.close()
     plan.close()
+
+
+@pytest.mark.parametrize("schedule", [1, 0, 2], ids=["fused", "phased", "grouped"])
+def test_batch_with_empty_scans(ctx, schedule):
+    """Scans without points (no rings, or no columns) inside a batch get zero
+    segments and leave their neighbours' results unchanged."""
+    lsg, batch = mods()
+    specs = mixed_specs(6, 7300)
+    scans = [lidarsim.make_scan(sp) for sp in specs]
+    shapes = [batch.ScanShape(s.rings, s.cols, sp.subsample) for sp, s in zip(specs, scans)]
+    # an empty scan first, in the middle and last
+    shapes = [batch.ScanShape(0, 64, 1)] + shapes[:3] + [batch.ScanShape(8, 0, 1)] + shapes[3:] + \
+        [batch.ScanShape(0, 0, 1)]
+    order = [None, 0, 1, 2, None, 3, 4, 5, None]
+    params = [params_of(specs[k]) if k is not None else lsg.Params() for k in order]
+    db = batch.DeviceBatch(shapes, params, 0)
+    for b, k in enumerate(order):
+        if k is not None:
+            db.set_scan(b, scans[k])
+    db.upload()
+    db.d_nseg.fill_(-1)
+    torch.cuda.synchronize()
+    plan = db.plan(ctx, lsg.TILES["32x120"])
+    plan.set_schedule(schedule)
+    plan.run()
+    torch.cuda.synchronize()
+    assert ctx.error() == lsg.LSG_OK
+    for b, k in enumerate(order):
+        mb, nrm, lab, nseg = db.view(b)
+        if k is None:
+            assert int(nseg.item()) == 0
+            continue
+        elev, xyzr = db.scan_inputs(b)
+        out = ctx.segment(elev, xyzr=xyzr, az0=scans[k].az0, daz=scans[k].daz, params=params_of(specs[k]))
+        torch.cuda.synchronize()
+        assert torch.equal(out.labels, lab) and torch.equal(out.nseg, nseg) and torch.equal(out.meshbits, mb)
+    plan.close()
