@@ -661,6 +661,7 @@ __device__ __forceinline__ void tile_components(const Loc& L, const uint8_t* __r
   int qn = 0;                                  // queued unions (warp-uniform)
   uint32_t prev = 0;                           // previous row's bytes of the lane's columns
   int psA = 0, psB = 0;                        // previous row's run starts (tile-linear)
+#pragma unroll 2  // consecutive rows' independent work overlaps
   for (int lr = 0; lr < L.rn; ++lr) {
     uint32_t cur = 0;
     if (act) cur = *reinterpret_cast<const uint16_t*>(tb + lr * TC + lcA);
@@ -745,6 +746,7 @@ __device__ __forceinline__ void tile_cross_and_roots(const Loc& L, const uint8_t
   const bool act = lane >= 1 && lane <= SO / 2;
   const size_t pitch = root_pitch(L.Ws);
   const uint16_t* rs = reinterpret_cast<const uint16_t*>(q + NW * QCAP) + w * TR * 32;  // C1's run starts
+#pragma unroll 2  // consecutive rows' independent work overlaps
   for (int lr = 0; lr < L.rn; ++lr) {
     const uint32_t cur = act ? *reinterpret_cast<const uint16_t*>(tb + lr * TC + lcA) : 0u;
     const uint32_t bA = cur & 0xffu, bB = cur >> 8;
