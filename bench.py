@@ -371,7 +371,8 @@ def spin_measurement(local, tile, reps=20, packets=16):
             last.append(e0.elapsed_time(e1))
     ctx.close()
     f, l = statistics.median(full), statistics.median(last)
-    return {"scan": f"{scan.rings}x{scan.cols} (128-ring template), {packets} packets", "tile": tile,
+    tile_name = "auto (per call)" if tile == lsg.LSG_TILE_AUTO else next(k for k, v in lsg.TILES.items() if v == tile)
+    return {"scan": f"{scan.rings}x{scan.cols} (128-ring template), {packets} packets", "tile": tile_name,
             "after_last_packet_ms": l, "full_pass_ms": f, "latency_cut": f / l}
 
 
@@ -519,13 +520,13 @@ def main():
         ms_plain = max_over_ranks(e0.elapsed_time(e1) / npl)
         plain = {"value": pts_all / (ms_plain / 1e3), "unit": UNIT, "ms_per_pass": ms_plain,
                  "scans_per_s": db.n * world / (ms_plain / 1e3),
-                 "gpu_launches_per_pass": 4 * db.n}
+                 "gpu_launches_per_pass": 4 * db.n, "tile": "auto (per call)"}
 
     # ---- served path: continuous batching of 8 sensors vs a serial loop ---
     served = None
     spin = None
     if not args.no_spin and rank == 0:
-        spin = spin_measurement(local, plan.tile)
+        spin = spin_measurement(local, lsg.LSG_TILE_AUTO)
     generator = None
     if not args.no_generator:
         generator = generator_measurement(specs, local, max(3, min(args.steps, 5)), 2, max_over_ranks,
@@ -551,6 +552,17 @@ def main():
             "algorithmic_bytes_per_launch": bpp * db.points,
             "traffic": (traffic_pp * db.points) if traffic_pp is not None else None}
     path_achieved = PATH_BYTES_PER_POINT * db.points / (ms_step / 1e3) / 1e9
+
+    # the path's roofline fraction of the other paths (the same 33 B/point)
+    def path_frac(points_per_s):
+        return PATH_BYTES_PER_POINT * points_per_s / 1e9 / peak
+
+    if plain is not None:
+        plain["path_roofline_frac"] = path_frac(plain["value"])
+    if served is not None:
+        for d in (served["batched"], served["serial_plain"], served["saturated"]["batched"],
+                  served["saturated"]["serial_plain"]):
+            d["path_roofline_frac"] = path_frac(d["points_per_s"])
 
     # ---- CPU baseline: the oracle on the host cores ------------------------
     cpu = None

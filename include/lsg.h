@@ -155,7 +155,8 @@ typedef struct {
 /* Tile shapes of the fused kernels: rows x columns of mesh vertices per CTA.
  * Each warp of a CTA sweeps a strip of 60 columns (two per lane) down the
  * tile's rows, so the widths are multiples of 60 (2 warps: 120, 4 warps:
- * 240, 8 warps: 480). */
+ * 240, 8 warps: 480).  LSG_TILE_AUTO: each call picks the shape from its
+ * work (see lsg_set_tile). */
 enum {
   LSG_TILE_AUTO = -1,
   LSG_TILE_16x240 = 0,
@@ -163,7 +164,8 @@ enum {
   LSG_TILE_32x240 = 2,
   LSG_TILE_32x480 = 3,
   LSG_TILE_64x240 = 4,
-  LSG_TILE_COUNT = 5
+  LSG_TILE_16x120 = 5,
+  LSG_TILE_COUNT = 6
 };
 
 /* Fills *p with the defaults listed above. */
@@ -180,7 +182,12 @@ lsg_status lsg_create(int device, size_t mem_budget_bytes, lsg_ctx** out);
 /* Frees the context and its workspace (synchronises the device first). */
 lsg_status lsg_destroy(lsg_ctx* ctx);
 
-/* Selects the tile shape used by lsg_segment (LSG_TILE_*; AUTO = default). */
+/* Selects the tile shape of the context's calls (lsg_segment,
+ * lsg_label_from_mask, lsg_batch_launch, lsg_spin_begin, and lsg_batch_plan
+ * given LSG_TILE_AUTO).  LSG_TILE_AUTO (the default) lets each call pick from
+ * its work: the first of 32x120, 32x240, 16x240, 16x120 that gives at least
+ * two tiles per SM, else the one that gives the most tiles (small scans fill
+ * the GPU with small tiles, large batches keep the efficient ones). */
 lsg_status lsg_set_tile(lsg_ctx* ctx, int tile);
 
 /*
@@ -217,8 +224,10 @@ lsg_status lsg_label_from_mask(lsg_ctx* ctx, int32_t H, int32_t W, int32_t s, in
  * replays to process new data of the same shapes.
  *   n          number of scans (>= 1)
  *   scans[n], params[n], outs[n]  as for lsg_segment (host arrays, copied)
- *   tile       LSG_TILE_* shape, or LSG_TILE_AUTO to let lsg_autotune pick
- *              later (the default shape is used until then).
+ *   tile       LSG_TILE_* shape, or LSG_TILE_AUTO: the context's shape if
+ *              lsg_set_tile fixed one, else the per-call choice described
+ *              at lsg_set_tile over the whole batch; lsg_autotune may
+ *              replace it later.
  */
 lsg_status lsg_batch_plan(lsg_ctx* ctx, int32_t n, const lsg_scan* scans, const lsg_params* params,
                           const lsg_out* outs, int tile, lsg_plan** plan);

@@ -31,7 +31,8 @@ struct lsg_ctx {
   void* ws = nullptr;       // single-scan / dynamic-batch workspace
   size_t ws_bytes = 0;
   int32_t* d_err = nullptr; // sticky device error word
-  int tile = LSG_TILE_32x240;
+  int tile = LSG_TILE_AUTO;  // or a fixed shape (lsg_set_tile)
+  int sms = 1;              // streaming multiprocessors of the device
   DynStage stage[2];        // alternated by successive lsg_batch_launch calls
   int next_stage = 0;
 };
@@ -194,6 +195,11 @@ lsg_status reserve(lsg_ctx* ctx, size_t need) {
   return LSG_OK;
 }
 
+// The context's tile shape for a call over scans of (rings, sampled columns).
+int ctx_tile(const lsg_ctx* ctx, const int* H, const int* Ws, int n) {
+  return ctx->tile >= 0 ? ctx->tile : pick_tile(H, Ws, n, ctx->sms);
+}
+
 lsg_status run_pass(const KArgs& a, int tile, bool geometry, cudaStream_t st) {
   cudaError_t e = launch_prep(a, st);
   if (e == cudaSuccess) e = geometry ? launch_tile(tile, a, st) : launch_tile_ccl(tile, a, st);
@@ -245,6 +251,8 @@ lsg_status lsg_create(int device, size_t mem_budget_bytes, lsg_ctx** out) {
   if (!c) return LSG_E_OOM;
   c->device = device;
   c->budget = mem_budget_bytes;
+  if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || c->sms < 1)
+    c->sms = 1;
   e = cudaMalloc(&c->d_err, 256);
   if (e != cudaSuccess) {
     delete c;
@@ -278,8 +286,7 @@ lsg_status lsg_destroy(lsg_ctx* ctx) {
 
 lsg_status lsg_set_tile(lsg_ctx* ctx, int tile) {
   if (!ctx) return LSG_E_ARG;
-  if (tile == LSG_TILE_AUTO) tile = LSG_TILE_32x240;
-  if (tile < 0 || tile >= LSG_TILE_COUNT) return LSG_E_ARG;
+  if (tile != LSG_TILE_AUTO && (tile < 0 || tile >= LSG_TILE_COUNT)) return LSG_E_ARG;
   ctx->tile = tile;
   return LSG_OK;
 }
@@ -296,15 +303,16 @@ lsg_status lsg_segment(lsg_ctx* ctx, const lsg_scan* scan, const lsg_params* par
     return cuda_status(cudaMemsetAsync(out->nseg, 0, sizeof(int32_t), cs));
   st = reserve(ctx, scan_ws_bytes(scan->rings, Ws));
   if (st != LSG_OK) return st;
+  const int tile = ctx_tile(ctx, &scan->rings, &Ws, 1);
   KArgs a;
   memset(&a, 0, sizeof(a));
   a.one = make_desc(scan, params, out, Ws);
-  set_tiles(a.one, ctx->tile, 0);
+  set_tiles(a.one, tile, 0);
   carve_ws(a.one, static_cast<char*>(ctx->ws));
   a.ntiles = a.one.tiles_r * a.one.tiles_c;
   a.nscans = 1;
   a.err = ctx->d_err;
-  return run_pass(a, ctx->tile, true, cs);
+  return run_pass(a, tile, true, cs);
 }
 
 lsg_status lsg_label_from_mask(lsg_ctx* ctx, int32_t H, int32_t W, int32_t s, int32_t wrap,
@@ -333,16 +341,17 @@ lsg_status lsg_label_from_mask(lsg_ctx* ctx, int32_t H, int32_t W, int32_t s, in
   d.valid = valid;
   d.labels = labels;
   d.nseg = nseg;
-  set_tiles(d, ctx->tile, 0);
+  const int tile = ctx_tile(ctx, &H, &Ws, 1);
+  set_tiles(d, tile, 0);
   carve_ws(d, static_cast<char*>(ctx->ws));
   a.ntiles = d.tiles_r * d.tiles_c;
   a.nscans = 1;
   a.err = ctx->d_err;
   // no elevations: the ring order is the identity and only nseg is reset
   cudaError_t e = cudaMemsetAsync(nseg, 0, sizeof(int32_t), cs);
-  if (e == cudaSuccess) e = launch_tile_ccl(ctx->tile, a, cs);
-  if (e == cudaSuccess) e = launch_merge(ctx->tile, a, cs);
-  if (e == cudaSuccess) e = launch_flatten(ctx->tile, a, cs);
+  if (e == cudaSuccess) e = launch_tile_ccl(tile, a, cs);
+  if (e == cudaSuccess) e = launch_merge(tile, a, cs);
+  if (e == cudaSuccess) e = launch_flatten(tile, a, cs);
   return cuda_status(e);
 }
 
@@ -410,17 +419,20 @@ lsg_status lsg_batch_launch_io(lsg_ctx* ctx, int32_t n, const lsg_scan* scans, c
 static lsg_status batch_launch(lsg_ctx* ctx, int32_t n, const lsg_scan* scans, const lsg_params* params,
                                const lsg_out* outs, const lsg_host_io* io, lsg_stream stream) {
   if (!ctx || n < 1 || !scans || !params || !outs) return LSG_E_ARG;
-  std::vector<int> Ws(n);
+  std::vector<int> Ws(n), Hs(n);
   size_t ws_total = 0;
   int64_t ntiles = 0;
-  const TileShape ts = tile_shape(ctx->tile);
   for (int b = 0; b < n; ++b) {
     lsg_status st = check_scan(&scans[b], &params[b], &outs[b], &Ws[b]);
     if (st != LSG_OK) return st;
     ws_total += scan_ws_bytes(scans[b].rings, Ws[b]);
-    if (scans[b].rings > 0 && scans[b].cols > 0)
-      ntiles += (int64_t)((scans[b].rings + ts.rows - 1) / ts.rows) * ((Ws[b] + ts.cols - 1) / ts.cols);
+    Hs[b] = scans[b].cols > 0 ? scans[b].rings : 0;
   }
+  const int tile = ctx_tile(ctx, Hs.data(), Ws.data(), n);
+  const TileShape ts = tile_shape(tile);
+  for (int b = 0; b < n; ++b)
+    if (Hs[b] > 0 && Ws[b] > 0)
+      ntiles += (int64_t)((Hs[b] + ts.rows - 1) / ts.rows) * ((Ws[b] + ts.cols - 1) / ts.cols);
   if (ntiles > INT32_MAX) return LSG_E_SHAPE;
   DeviceGuard g(ctx->device);
   cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
@@ -459,7 +471,7 @@ static lsg_status batch_launch(lsg_ctx* ctx, int32_t n, const lsg_scan* scans, c
     ScanDesc d = make_desc(&scans[b], &params[b], &outs[b], Ws[b]);
     carve_ws(d, base);
     base += scan_ws_bytes(d.H, d.Ws);
-    set_tiles(d, ctx->tile, t0);
+    set_tiles(d, tile, t0);
     const int nt = (d.H && d.W) ? d.tiles_r * d.tiles_c : 0;
     for (int k = 0; k < nt; ++k) htile[t0 + k] = b;
     t0 += nt;
@@ -476,9 +488,9 @@ static lsg_status batch_launch(lsg_ctx* ctx, int32_t n, const lsg_scan* scans, c
   a.nscans = n;
   a.err = ctx->d_err;
   e = launch_prep(a, cs);
-  if (e == cudaSuccess && t0 > 0) e = launch_tile(ctx->tile, a, cs);
-  if (e == cudaSuccess && t0 > 0) e = launch_merge(ctx->tile, a, cs);
-  if (e == cudaSuccess && t0 > 0) e = launch_flatten(ctx->tile, a, cs);
+  if (e == cudaSuccess && t0 > 0) e = launch_tile(tile, a, cs);
+  if (e == cudaSuccess && t0 > 0) e = launch_merge(tile, a, cs);
+  if (e == cudaSuccess && t0 > 0) e = launch_flatten(tile, a, cs);
   if (io) {
     // results device -> host, behind the pass
     for (int b = 0; b < n && e == cudaSuccess; ++b) {
@@ -682,14 +694,16 @@ lsg_status lsg_batch_plan(lsg_ctx* ctx, int32_t n, const lsg_scan* scans, const 
   if (!ctx || !plan || n < 1 || !scans || !params || !outs) return LSG_E_ARG;
   *plan = nullptr;
   if (tile == LSG_TILE_AUTO) tile = ctx->tile;
-  if (tile < 0 || tile >= LSG_TILE_COUNT) return LSG_E_ARG;
-  std::vector<int> Ws(n);
+  if (tile != LSG_TILE_AUTO && (tile < 0 || tile >= LSG_TILE_COUNT)) return LSG_E_ARG;
+  std::vector<int> Ws(n), Hs(n);
   size_t ws_total = 0;
   for (int b = 0; b < n; ++b) {
     lsg_status st = check_scan(&scans[b], &params[b], &outs[b], &Ws[b]);
     if (st != LSG_OK) return st;
     ws_total += scan_ws_bytes(scans[b].rings, Ws[b]);
+    Hs[b] = scans[b].cols > 0 ? scans[b].rings : 0;
   }
+  if (tile == LSG_TILE_AUTO) tile = pick_tile(Hs.data(), Ws.data(), n, ctx->sms);
   // bound on the tile table over every tile shape (at least 16 rows x 120 columns)
   size_t tiles_max = 0;
   for (int b = 0; b < n; ++b)
@@ -870,7 +884,7 @@ lsg_status lsg_spin_begin(lsg_ctx* ctx, const lsg_scan* scan, const lsg_params* 
   lsg_spin* sp = new (std::nothrow) lsg_spin();
   if (!sp) return LSG_E_OOM;
   sp->ctx = ctx;
-  sp->tile = ctx->tile;
+  sp->tile = ctx_tile(ctx, &scan->rings, &Ws, 1);
   memset(&sp->a, 0, sizeof(sp->a));
   sp->a.one = make_desc(scan, params, out, Ws);
   set_tiles(sp->a.one, sp->tile, 0);

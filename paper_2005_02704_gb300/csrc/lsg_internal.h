@@ -70,6 +70,11 @@ struct TileShape {
 };
 TileShape tile_shape(int tile);
 
+// Tile shape for a call whose scans are given by (rings, sampled columns):
+// the first of 32x120, 32x240, 16x240, 16x120 that yields at least two
+// tiles per SM, else the one that yields the most tiles.
+int pick_tile(const int* H, const int* Ws, int n, int sms);
+
 // Host helpers shared by the entry points (lsg_api.cu).
 lsg_status check_scan(const lsg_scan* sc, const lsg_params* p, const lsg_out* o, int* Ws_out);
 ScanDesc make_desc(const lsg_scan* sc, const lsg_params* p, const lsg_out* o, int Ws);

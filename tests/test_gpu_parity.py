@@ -94,6 +94,25 @@ def test_single_scan_workloads(ctx, make):
     assert rep.vertices > 0
 
 
+@pytest.mark.parametrize("make", [lidarsim.ring16, lidarsim.ring128],
+                         ids=["ring16x1800", "ring128x4096"])
+def test_auto_tile_equals_fixed(ctx, make):
+    """LSG_TILE_AUTO picks a shape per call; the outputs do not depend on it."""
+    lsg = lsg_mod()
+    spec = make()
+    scan = lidarsim.make_scan(spec)
+    p = params_of(spec)
+    lsg.lsg_set_tile(ctx.h, lsg.LSG_TILE_AUTO)
+    auto = run_gpu(ctx, scan, p)
+    lsg.lsg_set_tile(ctx.h, lsg.LSG_TILE_AUTO)
+    for tile in ("32x240", "16x120"):
+        fixed = run_gpu(ctx, scan, p, tile=lsg.TILES[tile])
+        for a, b in zip(auto, fixed):
+            assert np.array_equal(a, b), tile
+    with pytest.raises(lsg.LsgError):
+        lsg.lsg_set_tile(ctx.h, lsg.LSG_TILE_COUNT)
+
+
 def test_range_only_decode(ctx):
     spec = lidarsim.ring64(cols=1024)
     scan = lidarsim.make_scan(spec)
@@ -116,7 +135,7 @@ RAGGED = [
     (5, 1030, 1, 1, "32x240"), (33, 129, 1, 1, "64x240"), (16, 1800, 5, 1, "16x240"), (7, 1000, 15, 1, "32x480"),
     (64, 300, 1, 1, "32x120"), (3, 512, 2, 1, "32x240"), (24, 640, 4, 0, "64x240"),
     (8, 240, 1, 1, "16x240"), (8, 241, 1, 1, "16x240"), (5, 481, 1, 1, "32x480"), (3, 61, 1, 1, "32x120"),
-    (35, 121, 1, 0, "32x120"),
+    (35, 121, 1, 0, "32x120"), (17, 121, 1, 1, "16x120"), (33, 361, 2, 1, "16x120"), (16, 120, 1, 0, "16x120"),
 ]
 
 
@@ -196,7 +215,7 @@ def test_label_from_mask_random_masks(ctx):
             flat[hom] |= hb
         mb = flat.reshape(H, Ws)
         want, nwant = O.label_from_mask(mb, valid_full, W, s, wrap)
-        for tile in ("16x240", "32x120", "32x480"):
+        for tile in ("16x240", "32x120", "32x480", "16x120"):
             lsg.lsg_set_tile(ctx.h, lsg.TILES[tile])
             got, n = ctx.label_from_mask(torch.from_numpy(mb).to(dev), torch.from_numpy(valid_full).to(dev), W, s,
                                          wrap)
