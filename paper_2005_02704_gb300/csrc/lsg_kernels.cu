@@ -874,57 +874,75 @@ __device__ __forceinline__ int tile_root(const uint16_t* __restrict__ lroot, int
 // ---------------------------------------------------------------------------
 constexpr int NT_MERGE = 128;
 
-// Border unions of one tile (NTB threads).
+// Border unions of one tile (NTB threads, all of them calling).  Each lane
+// takes one border vertex and forms the pairs of tile roots its outgoing
+// homogeneous edges join, as (smaller, larger) scan-local indices.  Along a
+// border most pairs repeat (a component crossing it joins the same two tile
+// roots at every column), so each warp issues every distinct pair once.
 template <int TR, int NW, int NTB>
 __device__ __forceinline__ void merge_body(const ScanDesc* d, int lt, int32_t* err) {
+  static_assert(NTB % 32 == 0, "whole warps");
   constexpr int TC = NW * SO;
+  constexpr uint64_t NONE = ~0ull;
   const Loc L = make_loc(d, lt, TR, TC);
   const uint8_t* __restrict__ mb = d->mb;
   const uint16_t* __restrict__ lroot = d->lroot;
   int32_t* parent = d->parent;
   const int limit = L.H * L.Ws + 1;
   const bool full_ring = L.wrap && L.c0 == 0 && L.cn == L.Ws;
+  const size_t LP = root_pitch(L.Ws);
+  const int lane = threadIdx.x & 31;
   // border vertices: the last row of the tile, then the last column above it
   const int nb = L.cn + L.rn - 1;
-  for (int k = threadIdx.x; k < nb; k += NTB) {
-    int lr, lc;
-    if (k < L.cn) {
-      lr = L.rn - 1;
-      lc = k;
-    } else {
-      lr = k - L.cn;
-      lc = L.cn - 1;
+  for (int k0 = 0; k0 < nb; k0 += NTB) {  // trip count uniform over the block
+    const int k = k0 + (int)threadIdx.x;
+    uint64_t key[3] = {NONE, NONE, NONE};
+    if (k < nb) {
+      int lr, lc;
+      if (k < L.cn) {
+        lr = L.rn - 1;
+        lc = k;
+      } else {
+        lr = k - L.cn;
+        lc = L.cn - 1;
+      }
+      const int i = L.r0 + lr, j = L.c0 + lc;
+      const uint8_t bits = mb[(size_t)i * L.Ws + j];
+      // bits pointing off the grid (possible in a caller-given mask) are ignored
+      const bool has_right = (j + 1 < L.Ws) || L.wrap;
+      const bool has_down = i + 1 < L.H;
+      const int jn = (j + 1 == L.Ws) ? 0 : j + 1;
+      const bool jn_in = (lc + 1 < L.cn) || full_ring;
+      const bool down_in = lr + 1 < L.rn;
+      const bool hr_out = (bits & B_HR) && has_right && !jn_in;
+      const bool hd_out = (bits & B_HD) && has_down && !down_in;
+      const bool hg_out = (bits & B_HG) && has_down && has_right && !(down_in && jn_in);
+      if ((hr_out || hd_out || hg_out) && lroot[(size_t)i * LP + j] != NO_ROOT) {
+        const int rp = tile_root<TR, TC>(lroot, L.Ws, i, j);
+        auto pair = [rp](int rq) {
+          const uint32_t lo = (uint32_t)min(rp, rq), hi = (uint32_t)max(rp, rq);
+          return ((uint64_t)lo << 32) | hi;
+        };
+        if (hr_out && lroot[(size_t)i * LP + jn] != NO_ROOT)
+          key[0] = pair(tile_root<TR, TC>(lroot, L.Ws, i, jn));
+        if (hd_out && lroot[(size_t)(i + 1) * LP + j] != NO_ROOT)
+          key[1] = pair(tile_root<TR, TC>(lroot, L.Ws, i + 1, j));
+        if (hg_out && lroot[(size_t)(i + 1) * LP + jn] != NO_ROOT)
+          key[2] = pair(tile_root<TR, TC>(lroot, L.Ws, i + 1, jn));
+        if (key[1] == key[0]) key[1] = NONE;
+        if (key[2] == key[0] || key[2] == key[1]) key[2] = NONE;
+      }
     }
-    const int i = L.r0 + lr, j = L.c0 + lc;
-    const uint8_t bits = mb[(size_t)i * L.Ws + j];
-    if (!(bits & (B_HR | B_HD | B_HG))) continue;
-    // bits pointing off the grid (possible in a caller-given mask) are ignored
-    const bool has_right = (j + 1 < L.Ws) || L.wrap;
-    const bool has_down = i + 1 < L.H;
-    const int jn = (j + 1 == L.Ws) ? 0 : j + 1;
-    const bool jn_in = (lc + 1 < L.cn) || full_ring;
-    const bool down_in = lr + 1 < L.rn;
-    const bool hr_out = (bits & B_HR) && has_right && !jn_in;
-    const bool hd_out = (bits & B_HD) && has_down && !down_in;
-    const bool hg_out = (bits & B_HG) && has_down && has_right && !(down_in && jn_in);
-    if (!(hr_out || hd_out || hg_out)) continue;
-    const size_t LP = root_pitch(L.Ws);
-    if (lroot[(size_t)i * LP + j] == NO_ROOT) continue;
-    // along the bottom border, a D edge whose two tile roots equal those of
-    // the left neighbour's D edge adds nothing
-    if (hd_out && !hr_out && !hg_out && k > 0 && k < L.cn) {
-      const uint8_t bl = mb[(size_t)i * L.Ws + j - 1];
-      if ((bl & B_HD) && lroot[(size_t)i * LP + j - 1] == lroot[(size_t)i * LP + j] &&
-          lroot[(size_t)(i + 1) * LP + j - 1] == lroot[(size_t)(i + 1) * LP + j])
-        continue;
+    // a diagonal pair often repeats the next lane's down pair (bottom row)
+    // or right pair (right column): that lane's round joins it
+    const uint64_t nd = __shfl_down_sync(FULL, key[1], 1), nr = __shfl_down_sync(FULL, key[0], 1);
+    if (lane < 31 && (key[2] == nd || key[2] == nr)) key[2] = NONE;
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      const unsigned same = __match_any_sync(FULL, key[e]);
+      if (key[e] != NONE && lane == __ffs(same) - 1)
+        union_g(parent, (int)(key[e] >> 32), (int)(key[e] & 0xffffffffu), limit, err);
     }
-    const int rp = tile_root<TR, TC>(lroot, L.Ws, i, j);
-    if (hr_out && lroot[(size_t)i * LP + jn] != NO_ROOT)
-      union_g(parent, rp, tile_root<TR, TC>(lroot, L.Ws, i, jn), limit, err);
-    if (hd_out && lroot[(size_t)(i + 1) * LP + j] != NO_ROOT)
-      union_g(parent, rp, tile_root<TR, TC>(lroot, L.Ws, i + 1, j), limit, err);
-    if (hg_out && lroot[(size_t)(i + 1) * LP + jn] != NO_ROOT)
-      union_g(parent, rp, tile_root<TR, TC>(lroot, L.Ws, i + 1, jn), limit, err);
   }
 }
 
