@@ -1084,22 +1084,19 @@ __device__ __forceinline__ void flatten_body(const ScanDesc* d, int lt, unsigned
   //     at a time (independent loads in flight)
   int nroots = 0;
   const int nl = nlist;
+  auto scan_index = [&](int v) { return (L.r0 + v / TC) * Ws + L.c0 + v % TC; };
   for (int k0 = tid; k0 < nl; k0 += 4 * NTB) {
-    int x[4], gv[4];
-    bool live[4];
+    int x[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int k = k0 + q * NTB;
-      live[q] = k < nl;
-      const int v = live[q] ? list_s[k] : 0;
-      gv[q] = (L.r0 + v / TC) * Ws + L.c0 + v % TC;
-      x[q] = gv[q];
+      x[q] = scan_index(k < nl ? list_s[k] : 0);
     }
     for (int it = 0; it < limit; ++it) {
       bool more = false;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        if (!live[q]) continue;
+        if (k0 + q * NTB >= nl) continue;
         const int p = __ldg(parent + x[q]);
         if (p != x[q]) {
           x[q] = p;
@@ -1110,11 +1107,12 @@ __device__ __forceinline__ void flatten_body(const ScanDesc* d, int lt, unsigned
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      if (!live[q]) continue;
-      const int g = x[q];
-      nroots += (g == gv[q]);
+      const int k = k0 + q * NTB;
+      if (k >= nl) continue;
+      const int v = list_s[k], g = x[q];
+      nroots += (g == scan_index(v));
       const int gi = g / Ws, gj = g - gi * Ws;
-      lab_s[list_s[k0 + q * NTB]] = gi * W + gj * s;
+      lab_s[v] = gi * W + gj * s;
     }
   }
   const int cnt = __reduce_add_sync(FULL, nroots);
@@ -1184,8 +1182,17 @@ __device__ __forceinline__ void flatten_body(const ScanDesc* d, int lt, unsigned
   }
 }
 
+// CTAs of k_flatten per SM: as many as the shared memory holds, at most six
+// (the phases wait on loads, so resident tiles hide each other's latency;
+// six leaves 40 registers a thread).
 template <int TR, int NW>
-__global__ void __launch_bounds__(NT_FLAT) k_flatten(const __grid_constant__ KArgs a) {
+constexpr int flat_min_blocks() {
+  constexpr int n = (int)((220u * 1024u) / FlatGeo<TR, NW>::bytes);
+  return n < 1 ? 1 : (n > 6 ? 6 : n);
+}
+
+template <int TR, int NW>
+__global__ void __launch_bounds__(NT_FLAT, (flat_min_blocks<TR, NW>())) k_flatten(const __grid_constant__ KArgs a) {
   extern __shared__ __align__(16) unsigned char fsm[];
   __shared__ int nlist;
   for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
