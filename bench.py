@@ -461,20 +461,28 @@ def main():
     # (a) the pipelined host path: chunks of scans whose copies in both
     #     directions overlap the other chunks' passes; (b) for reference, the
     #     same copies and the single-plan pass queued one after the other
+    #     The host loop runs with the cyclic collector paused; the median of
+    #     three timed regions of K steps each is reported (host-side jitter
+    #     stretches single regions)
+    from paper_2005_02704_gb300 import serve
     pipe = db.pipeline(ctx, plan.tile, chunks=args.e2e_chunks, schedule=schedule)
     for _ in range(max(args.warmup, 3)):
         pipe.step(stream)
-    torch.cuda.synchronize()
-    barrier()
-    torch.cuda.synchronize()
-    e0.record(stream)
     h2d = d2h = 0
-    for _ in range(args.steps):
-        h2d, d2h = pipe.step(stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    ms_e2e = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+    regions = []
+    with serve.no_gc_pauses():
+        for _ in range(3):
+            torch.cuda.synchronize()
+            barrier()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(args.steps):
+                h2d, d2h = pipe.step(stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            barrier()
+            regions.append(max_over_ranks(e0.elapsed_time(e1) / args.steps))
+    ms_e2e = statistics.median(regions)
     e2e_value = pts_all / (ms_e2e / 1e3)
     pipe.close()
     for _ in range(max(args.warmup, 3)):
@@ -512,13 +520,18 @@ def main():
         torch.cuda.synchronize()
         barrier()
         npl = max(2, min(args.steps, 5))
-        e0.record(stream)
-        for _ in range(npl):
-            plain_pass()
-        e1.record(stream)
-        torch.cuda.synchronize()
+        from paper_2005_02704_gb300 import serve
+        with serve.no_gc_pauses():
+            e0.record(stream)
+            t0 = time.perf_counter()
+            for _ in range(npl):
+                plain_pass()
+            host_ms = (time.perf_counter() - t0) * 1e3 / npl  # enqueue time of the 512 calls
+            e1.record(stream)
+            torch.cuda.synchronize()
         ms_plain = max_over_ranks(e0.elapsed_time(e1) / npl)
         plain = {"value": pts_all / (ms_plain / 1e3), "unit": UNIT, "ms_per_pass": ms_plain,
+                 "host_enqueue_ms_per_pass": host_ms,
                  "scans_per_s": db.n * world / (ms_plain / 1e3),
                  "gpu_launches_per_pass": 4 * db.n, "tile": "auto (per call)"}
 
@@ -594,6 +607,7 @@ def main():
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": ms_e2e, "path": f"HostPipeline, {args.e2e_chunks} chunks, 3 streams",
+                    "ms_per_step_regions": regions,
                     "serial_ms_per_step": ms_e2e_serial,
                     "serial_value": pts_all / (ms_e2e_serial / 1e3)},
             "plain": plain,

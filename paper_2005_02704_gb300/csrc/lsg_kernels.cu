@@ -872,7 +872,12 @@ __device__ __forceinline__ int tile_root(const uint16_t* __restrict__ lroot, int
 // ---------------------------------------------------------------------------
 // k_merge: join components across tile borders and the 360 deg seam
 // ---------------------------------------------------------------------------
-constexpr int NT_MERGE = 128;
+// threads of k_merge: one per border vertex of a tile (the last row and the
+// last column), rounded up to whole warps
+template <int TR, int NW>
+__host__ __device__ constexpr int nt_merge() {
+  return ((NW * SO + TR - 1 + 31) / 32) * 32;
+}
 
 // Border unions of one tile (NTB threads, all of them calling).  Each lane
 // takes one border vertex and forms the pairs of tile roots its outgoing
@@ -947,11 +952,11 @@ __device__ __forceinline__ void merge_body(const ScanDesc* d, int lt, int32_t* e
 }
 
 template <int TR, int NW>
-__global__ void __launch_bounds__(NT_MERGE) k_merge(const __grid_constant__ KArgs a) {
+__global__ void __launch_bounds__(nt_merge<TR, NW>()) k_merge(const __grid_constant__ KArgs a) {
   for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
     int lt;
     const ScanDesc* d = tile_desc(a, t, lt);
-    merge_body<TR, NW, NT_MERGE>(d, lt, a.err);
+    merge_body<TR, NW, nt_merge<TR, NW>()>(d, lt, a.err);
   }
 }
 
@@ -1326,7 +1331,7 @@ static cudaError_t run_tile_ccl(const KArgs& a, cudaStream_t st) {
 }
 template <int TR, int NW>
 static cudaError_t run_merge(const KArgs& a, cudaStream_t st) {
-  k_merge<TR, NW><<<a.ntiles, NT_MERGE, 0, st>>>(a);
+  k_merge<TR, NW><<<a.ntiles, nt_merge<TR, NW>(), 0, st>>>(a);
   return cudaGetLastError();
 }
 template <int TR, int NW>
