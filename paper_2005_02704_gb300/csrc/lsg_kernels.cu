@@ -1116,8 +1116,12 @@ __device__ __forceinline__ void flatten_body(const ScanDesc* d, int lt, unsigned
       if (k >= nl) continue;
       const int v = list_s[k], g = x[q];
       nroots += (g == scan_index(v));
-      const int gi = g / Ws, gj = g - gi * Ws;
-      lab_s[v] = gi * W + gj * s;
+      int lab = g;  // s = 1: W = Ws, so the point index is the vertex index
+      if (s != 1) {
+        const int gi = g / Ws, gj = g - gi * Ws;
+        lab = gi * W + gj * s;
+      }
+      lab_s[v] = lab;
     }
   }
   const int cnt = __reduce_add_sync(FULL, nroots);
