@@ -417,6 +417,7 @@ def main():
     if args.grouped:
         plan.set_schedule(2)
     schedule = plan.schedule
+    launches_per_pass = plan.launches  # kernel launches in one replay (grouped: 1 + 3 per scan group)
     tile_name = {v: k for k, v in lsg.TILES.items()}[plan.tile]
 
     # ---- batched path, inputs resident ------------------------------------
@@ -615,7 +616,7 @@ def main():
             "generator": generator,
             "streaming": spin,
             "scans_per_s": db.n * world / (ms_step / 1e3),
-            "gpu_launches": (1 if fused else 4) * args.steps,
+            "gpu_launches": launches_per_pass * args.steps,
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)

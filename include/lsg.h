@@ -298,6 +298,11 @@ lsg_status lsg_plan_set_fused(lsg_plan* plan, int fused);
 /* The plan's schedule (0, 1 or 2, see lsg_plan_set_fused). */
 int lsg_plan_fused(const lsg_plan* plan);
 
+/* Kernel launches in one lsg_batch_run of the plan as captured now (phased:
+ * 4, fused: 1, grouped: 1 + 3 per scan group; 1 when no scan has points);
+ * -1 for a null plan. */
+int lsg_plan_launches(const lsg_plan* plan);
+
 /* Device time of each phase of the plan's last replay, in milliseconds.
  * Phased plans: ms[0] ring order, ms[1] tile kernel (decode, mesh, normals,
  * edge mask, tile-local components), ms[2] border merge, ms[3] labels and

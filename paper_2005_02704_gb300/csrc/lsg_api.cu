@@ -54,6 +54,7 @@ struct lsg_plan {
   int2* d_items = nullptr;          // fused schedule
   int32_t nitems = 0;
   int32_t* d_counters = nullptr;    // [1 + 3n] fused progress counters
+  int launches = 0;                 // kernel launches in one replay of the graph
 };
 
 namespace {
@@ -611,6 +612,7 @@ static lsg_status plan_capture(lsg_plan* pl) {
   }
   if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   lsg_status st = LSG_OK;
+  int launches = 0;
   if (e == cudaSuccess) {
     // scans with no points only get their counter cleared (by k_prep, which
     // runs one block per scan); the tile kernels see only non-empty scans.
@@ -622,6 +624,7 @@ static lsg_status plan_capture(lsg_plan* pl) {
       // group's tiles finish, its latency-bound merge and labels run beside
       // the other groups' tile work
       if (le == cudaSuccess) le = launch_prep(a, cs);
+      launches = 1;
       if (le == cudaSuccess) le = cudaEventRecordWithFlags(pl->ev[1], cs, cudaEventRecordExternal);
       if (le == cudaSuccess) le = cudaEventRecord(fork[0], cs);
       int b0 = 0;
@@ -642,6 +645,7 @@ static lsg_status plan_capture(lsg_plan* pl) {
         if (le == cudaSuccess) le = launch_tile(pl->tile, ag, side[g]);
         if (le == cudaSuccess) le = launch_merge(pl->tile, ag, side[g]);
         if (le == cudaSuccess) le = launch_flatten(pl->tile, ag, side[g]);
+        launches += 3;
         if (le == cudaSuccess) le = cudaEventRecord(join[g], side[g]);
         if (b0 >= pl->n) break;
       }
@@ -662,6 +666,7 @@ static lsg_status plan_capture(lsg_plan* pl) {
       if (le == cudaSuccess) le = cudaMemsetAsync(pl->d_counters, 0, sizeof(int32_t) * (1 + 3 * (size_t)pl->n), cs);
       if (le == cudaSuccess) le = cudaEventRecordWithFlags(pl->ev[1], cs, cudaEventRecordExternal);
       if (le == cudaSuccess) le = launch_fused(pl->tile, f, cs);
+      launches = 1;
       if (le == cudaSuccess) le = cudaEventRecordWithFlags(pl->ev[2], cs, cudaEventRecordExternal);
       if (le == cudaSuccess) le = cudaEventRecordWithFlags(pl->ev[3], cs, cudaEventRecordExternal);
       if (le == cudaSuccess) le = cudaEventRecordWithFlags(pl->ev[4], cs, cudaEventRecordExternal);
@@ -674,12 +679,14 @@ static lsg_status plan_capture(lsg_plan* pl) {
       if (le == cudaSuccess) le = cudaEventRecordWithFlags(pl->ev[3], cs, cudaEventRecordExternal);
       if (le == cudaSuccess && pl->ntiles > 0) le = launch_flatten(pl->tile, a, cs);
       if (le == cudaSuccess) le = cudaEventRecordWithFlags(pl->ev[4], cs, cudaEventRecordExternal);
+      launches = pl->ntiles > 0 ? 4 : 1;
     }
     e = cudaStreamEndCapture(cs, &pl->graph);
     if (le != cudaSuccess) e = le;
   }
   if (e == cudaSuccess) e = cudaGraphInstantiate(&pl->exec, pl->graph, 0);
   st = cuda_status(e);
+  pl->launches = st == LSG_OK ? launches : 0;
   for (int g = 0; g < kGroups; ++g) {
     if (side[g]) cudaStreamDestroy(side[g]);
     if (fork[g]) cudaEventDestroy(fork[g]);
@@ -818,6 +825,8 @@ lsg_status lsg_autotune(lsg_plan* plan, int reps, lsg_stream stream, int* best_t
 }
 
 int lsg_plan_fused(const lsg_plan* plan) { return plan ? plan->fused : -1; }
+
+int lsg_plan_launches(const lsg_plan* plan) { return plan ? plan->launches : -1; }
 
 lsg_status lsg_plan_destroy(lsg_plan* plan) {
   if (!plan) return LSG_E_ARG;

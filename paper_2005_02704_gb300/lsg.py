@@ -99,6 +99,7 @@ def load(build: bool = True):
             "lsg_plan_tile": (ctypes.c_int, [_P]),
             "lsg_plan_set_fused": (ctypes.c_int, [_P, ctypes.c_int]),
             "lsg_plan_fused": (ctypes.c_int, [_P]),
+            "lsg_plan_launches": (ctypes.c_int, [_P]),
             "lsg_plan_phase_times": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float)]),
             "lsg_plan_destroy": (ctypes.c_int, [_P]),
             "lsg_get_error": (ctypes.c_int, [_P]),
@@ -481,6 +482,11 @@ class BatchPlan:
     @property
     def fused(self) -> bool:
         return load().lsg_plan_fused(self.h) == 1
+
+    @property
+    def launches(self) -> int:
+        """Kernel launches in one run of the plan."""
+        return load().lsg_plan_launches(self.h)
 
     def phase_times(self):
         """[ring order, tile kernel, border merge, labels] ms of the last replay."""

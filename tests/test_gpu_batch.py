@@ -186,6 +186,11 @@ def test_batch_with_empty_scans(ctx, schedule):
     torch.cuda.synchronize()
     plan = db.plan(ctx, lsg.TILES["32x120"])
     plan.set_schedule(schedule)
+    # kernel launches per run: phased 4, fused 1, grouped ring order + 3 per scan group
+    if schedule == 2:
+        assert plan.launches in (4, 7, 10, 13)
+    else:
+        assert plan.launches == (1 if schedule == 1 else 4)
     plan.run()
     torch.cuda.synchronize()
     assert ctx.error() == lsg.LSG_OK
