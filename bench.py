@@ -66,6 +66,7 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-generator", action="store_true", help="skip timing the GPU scan generator")
     ap.add_argument("--no-spin", action="store_true", help="skip the streaming (per-packet) latency measurement")
+    ap.add_argument("--no-single", action="store_true", help="skip the single-scan latency measurement")
     ap.add_argument("--phased", action="store_true", help="force four phased launches (else the autotuner's choice)")
     ap.add_argument("--fused", action="store_true", help="force the single persistent launch")
     ap.add_argument("--grouped", action="store_true", help="force the grouped schedule")
@@ -330,6 +331,94 @@ def generator_measurement(specs, local, steps, warmup, max_over_ranks, sum_over_
             "ms_per_batch": ms, "rays_per_s": sum_over_ranks(total) / (ms / 1e3), "launches_per_batch": len(jobs)}
 
 
+SINGLE_SCANS = (("ring16x1800", "ring16"), ("ring64x2048_s2", "ring64"), ("ring128x4096", "ring128"))
+
+
+def pct(sorted_vals, q):
+    """q-quantile of sorted values (nearest rank)."""
+    return sorted_vals[min(len(sorted_vals) - 1, max(0, int(math.ceil(q * len(sorted_vals))) - 1))]
+
+
+def single_scan_measurement(local, peak, reps=100, warm=10):
+    """The three single-scan workloads (16 x 1800; 64 x 2048 at s = 2;
+    128 x 4096) through lsg_segment, tile shape chosen per call: device
+    latency of each of `reps` back-to-back calls (events around each call on
+    the launching stream), p50 / p99, points/s at the median and the path's
+    algorithmic bytes (8 + 25/s per point) against HBM.  Each scan (at most
+    8.4 MB of input) stays resident in the 129 MB L2 between calls."""
+    import torch
+
+    import lidarsim
+    from paper_2005_02704_gb300 import lsg
+    dev = torch.device("cuda", local)
+    ctx = lsg.Context(local)
+    stream = torch.cuda.current_stream()
+    res = {}
+    for name, maker in SINGLE_SCANS:
+        spec = getattr(lidarsim, maker)()
+        scan = lidarsim.make_scan(spec)
+        p = seg_params(spec)
+        elev = torch.from_numpy(scan.elev).to(dev)
+        xyzr = torch.from_numpy(scan.xyzr).to(dev)
+        out = lsg.alloc_outputs(scan.rings, scan.cols, spec.subsample, dev)
+
+        def call():
+            ctx.segment(elev, xyzr=xyzr, az0=scan.az0, daz=scan.daz, params=p, out=out, stream=stream)
+
+        for _ in range(warm):
+            call()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        torch.cuda.synchronize()
+        for a, b in ev:
+            a.record(stream)
+            call()
+            b.record(stream)
+        torch.cuda.synchronize()
+        if ctx.error() != lsg.LSG_OK:
+            raise RuntimeError("device error in the single-scan measurement")
+        t = sorted(a.elapsed_time(b) for a, b in ev)
+        p50, p99 = pct(t, 0.5), pct(t, 0.99)
+        n = scan.rings * scan.cols
+        bpp = 8.0 + 25.0 / spec.subsample
+        res[name] = {"points": n, "subsample": spec.subsample, "p50_ms": p50, "p99_ms": p99,
+                     "points_per_s": n / (p50 / 1e3), "scans_per_s": 1e3 / p50, "bytes_per_point": bpp,
+                     "achieved_gbs": bpp * n / (p50 / 1e3) / 1e9,
+                     "hbm_frac": bpp * n / (p50 / 1e3) / 1e9 / peak}
+    ctx.close()
+    res["note"] = (f"{reps} back-to-back lsg_segment calls per scan after {warm} warm-up calls, tile shape per call; "
+                   "L2-resident (latency-bound, not HBM-bound)")
+    return res
+
+
+def oracle_single_scans(reps=3):
+    """The oracle's single-threaded time per single-scan workload (median of
+    `reps` runs)."""
+    import lidarsim
+    import oracle as O
+    res = {}
+    for name, maker in SINGLE_SCANS:
+        spec = getattr(lidarsim, maker)()
+        scan = lidarsim.make_scan(spec)
+        p = O.Params(subsample=spec.subsample, r_max=spec.r_max, jump_rel_h=spec.jump_rel_h,
+                     jump_rel_v=spec.jump_rel_v, angle_rad=math.radians(spec.angle_deg))
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            O.segment_scan(scan, p)
+            ts.append((time.perf_counter() - t0) * 1e3)
+        ms = statistics.median(ts)
+        res[name] = {"ms": ms, "points_per_s": scan.rings * scan.cols / (ms / 1e3)}
+    return res
+
+
+# The paper's own timings (Table 1: C++ on one 7th-generation i5 core, 32 x
+# 1800 scans of 57,600 points), context only
+PAPER_TABLE1 = {"hardware": "7th-generation Intel i5, DDR4 8 GB, C++ (thread count and precision not stated)",
+                "scan": "32 x 1800 (57,600 points), simulated Velodyne 32E",
+                "ms_per_scan": {"s=5": 54.33, "s=10": 35.06, "s=15": 25.53},
+                "points_per_s": {"s=5": 57600 / 54.33e-3, "s=10": 57600 / 35.06e-3, "s=15": 57600 / 25.53e-3}}
+
+
 def spin_measurement(local, tile, reps=20, packets=16):
     """Streaming: a 128 x 4096 scan (the 128-ring template, 0.088 deg) pushed
     in `packets` column ranges; device time from the last packet to labels
@@ -442,6 +531,15 @@ def main():
         raise RuntimeError("device error during the timed region")
     pts_all = sum_over_ranks(float(db.points))
     value = pts_all / (ms_step / 1e3)
+    # per-pass latency distribution: 100 single replays, events around each
+    lat_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(100)]
+    for a, b in lat_ev:
+        a.record(stream)
+        plan.run()
+        b.record(stream)
+    torch.cuda.synchronize()
+    lat = sorted(a.elapsed_time(b) for a, b in lat_ev)
+    batched_latency = {"p50_ms": pct(lat, 0.5), "p99_ms": pct(lat, 0.99), "passes": len(lat)}
 
     # ---- per-phase device times (events recorded inside the graph) ---------
     # (the grouped schedule overlaps its kernels, so its per-kernel times are
@@ -541,6 +639,9 @@ def main():
     spin = None
     if not args.no_spin and rank == 0:
         spin = spin_measurement(local, lsg.LSG_TILE_AUTO)
+    singles = None
+    if not args.no_single and rank == 0:
+        singles = single_scan_measurement(local, measured_hbm()[0])
     generator = None
     if not args.no_generator:
         generator = generator_measurement(specs, local, max(3, min(args.steps, 5)), 2, max_over_ranks,
@@ -587,7 +688,8 @@ def main():
         r, pts, ns, dt = oracle_rate(specs, scans, float(db.points), cores)
         cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{ns} of the 512 scans (every {math.ceil(len(scans) / ns)}th), {pts / 1e6:.1f} M points, "
-                         f"{dt:.1f} s wall on {cores} threads"}
+                         f"{dt:.1f} s wall on {cores} threads",
+               "single_scans_one_thread": oracle_single_scans() if not args.no_single else None}
 
     if rank == 0:
         line = {
@@ -611,10 +713,13 @@ def main():
                     "ms_per_step_regions": regions,
                     "serial_ms_per_step": ms_e2e_serial,
                     "serial_value": pts_all / (ms_e2e_serial / 1e3)},
+            "batched_latency": batched_latency,
             "plain": plain,
+            "single_scans": singles,
             "served": served,
             "generator": generator,
             "streaming": spin,
+            "paper_table1": PAPER_TABLE1,
             "scans_per_s": db.n * world / (ms_step / 1e3),
             "gpu_launches": launches_per_pass * args.steps,
             "clocks": clk,
