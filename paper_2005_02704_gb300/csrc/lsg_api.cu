@@ -202,10 +202,11 @@ int ctx_tile(const lsg_ctx* ctx, const int* H, const int* Ws, int n) {
 }
 
 lsg_status run_pass(const KArgs& a, int tile, bool geometry, cudaStream_t st) {
+  // the three kernels after k_prep start while their predecessor drains
   cudaError_t e = launch_prep(a, st);
-  if (e == cudaSuccess) e = geometry ? launch_tile(tile, a, st) : launch_tile_ccl(tile, a, st);
-  if (e == cudaSuccess) e = launch_merge(tile, a, st);
-  if (e == cudaSuccess) e = launch_flatten(tile, a, st);
+  if (e == cudaSuccess) e = geometry ? launch_tile(tile, a, st, true) : launch_tile_ccl(tile, a, st, true);
+  if (e == cudaSuccess) e = launch_merge(tile, a, st, true);
+  if (e == cudaSuccess) e = launch_flatten(tile, a, st, true);
   return cuda_status(e);
 }
 
@@ -351,8 +352,8 @@ lsg_status lsg_label_from_mask(lsg_ctx* ctx, int32_t H, int32_t W, int32_t s, in
   // no elevations: the ring order is the identity and only nseg is reset
   cudaError_t e = cudaMemsetAsync(nseg, 0, sizeof(int32_t), cs);
   if (e == cudaSuccess) e = launch_tile_ccl(tile, a, cs);
-  if (e == cudaSuccess) e = launch_merge(tile, a, cs);
-  if (e == cudaSuccess) e = launch_flatten(tile, a, cs);
+  if (e == cudaSuccess) e = launch_merge(tile, a, cs, true);
+  if (e == cudaSuccess) e = launch_flatten(tile, a, cs, true);
   return cuda_status(e);
 }
 
@@ -489,9 +490,9 @@ static lsg_status batch_launch(lsg_ctx* ctx, int32_t n, const lsg_scan* scans, c
   a.nscans = n;
   a.err = ctx->d_err;
   e = launch_prep(a, cs);
-  if (e == cudaSuccess && t0 > 0) e = launch_tile(tile, a, cs);
-  if (e == cudaSuccess && t0 > 0) e = launch_merge(tile, a, cs);
-  if (e == cudaSuccess && t0 > 0) e = launch_flatten(tile, a, cs);
+  if (e == cudaSuccess && t0 > 0) e = launch_tile(tile, a, cs, true);
+  if (e == cudaSuccess && t0 > 0) e = launch_merge(tile, a, cs, true);
+  if (e == cudaSuccess && t0 > 0) e = launch_flatten(tile, a, cs, true);
   if (io) {
     // results device -> host, behind the pass
     for (int b = 0; b < n && e == cudaSuccess; ++b) {

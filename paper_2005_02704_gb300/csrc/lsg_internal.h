@@ -82,10 +82,13 @@ void set_tiles(ScanDesc& d, int tile, int tile0);
 
 // Kernel launchers (lsg_kernels.cu).  All return the launch error.
 cudaError_t launch_prep(const KArgs& a, cudaStream_t st);
-cudaError_t launch_tile(int tile, const KArgs& a, cudaStream_t st);
-cudaError_t launch_tile_ccl(int tile, const KArgs& a, cudaStream_t st);
-cudaError_t launch_merge(int tile, const KArgs& a, cudaStream_t st);
-cudaError_t launch_flatten(int tile, const KArgs& a, cudaStream_t st);
+// pdl: launch as a programmatic dependent of the previous kernel in the
+// stream (which must be one of these kernels or k_prep of the same pass), so
+// its CTAs are scheduled while that kernel drains.  Not for graph capture.
+cudaError_t launch_tile(int tile, const KArgs& a, cudaStream_t st, bool pdl = false);
+cudaError_t launch_tile_ccl(int tile, const KArgs& a, cudaStream_t st, bool pdl = false);
+cudaError_t launch_merge(int tile, const KArgs& a, cudaStream_t st, bool pdl = false);
+cudaError_t launch_flatten(int tile, const KArgs& a, cudaStream_t st, bool pdl = false);
 cudaError_t launch_fused(int tile, const FusedArgs& f, cudaStream_t st);
 cudaError_t prepare_kernels();  // one-time function attributes
 

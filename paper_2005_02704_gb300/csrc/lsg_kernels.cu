@@ -88,6 +88,16 @@ int pick_tile(const int* H, const int* Ws, int n, int sms) {
 // ---------------------------------------------------------------------------
 // small device helpers
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch: a kernel launched with the programmatic
+// stream serialization attribute may be scheduled while the kernel before it
+// in the stream is still running.  dep_wait blocks until that kernel has
+// completed and its memory writes are visible (it returns at once for a
+// kernel launched without the attribute); every kernel calls it before it
+// reads anything.  dep_release lets the next kernel be scheduled now (it
+// still waits in its own dep_wait).
+__device__ __forceinline__ void dep_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void dep_release() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
 __device__ __forceinline__ bool in_range(float r, float rmin, float rmax) {
   return rmin < r && r <= rmax;
 }
@@ -206,6 +216,8 @@ __device__ __forceinline__ void prep_body(const ScanDesc* d, float* se, int32_t*
 
 __global__ void __launch_bounds__(NT_PREP) k_prep(const __grid_constant__ KArgs a) {
   __shared__ float se[LSG_MAX_RINGS];
+  dep_wait();
+  dep_release();
   prep_body<NT_PREP>(a.scans ? a.scans + blockIdx.x : &a.one, se, a.err);
 }
 
@@ -827,6 +839,8 @@ __device__ __forceinline__ void tile_body(const ScanDesc* d, int lt, unsigned ch
 template <int TR, int NW>
 __global__ void __launch_bounds__(NW * 32, 16 / NW) k_tile(const __grid_constant__ KArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
+  dep_wait();
+  dep_release();
   for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
     int lt;
     const ScanDesc* d = tile_desc(a, t, lt);
@@ -843,6 +857,8 @@ __global__ void __launch_bounds__(NW * 32) k_tile_ccl(const __grid_constant__ KA
   using G = Geo<TR, NW>;
   constexpr int TC = G::TC;
   extern __shared__ __align__(16) unsigned char smem[];
+  dep_wait();
+  dep_release();
   int* lp = reinterpret_cast<int*>(smem);
   uint8_t* tb = smem + G::lp_bytes;
   uint32_t* q = reinterpret_cast<uint32_t*>(smem + G::lp_bytes + ((G::NV + 15) / 16) * 16);
@@ -955,6 +971,8 @@ __device__ __forceinline__ void merge_body(const ScanDesc* d, int lt, int32_t* e
 
 template <int TR, int NW>
 __global__ void __launch_bounds__(nt_merge<TR, NW>()) k_merge(const __grid_constant__ KArgs a) {
+  dep_wait();
+  dep_release();
   for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
     int lt;
     const ScanDesc* d = tile_desc(a, t, lt);
@@ -1206,6 +1224,7 @@ template <int TR, int NW>
 __global__ void __launch_bounds__(NT_FLAT, (flat_min_blocks<TR, NW>())) k_flatten(const __grid_constant__ KArgs a) {
   extern __shared__ __align__(16) unsigned char fsm[];
   __shared__ int nlist;
+  dep_wait();
   for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
     int lt;
     const ScanDesc* d = tile_desc(a, t, lt);
@@ -1310,6 +1329,23 @@ cudaError_t prepare_kernels() {
   return cudaSuccess;
 }
 
+// Launch of a kernel taking KArgs; with pdl, as a programmatic dependent of
+// the kernel before it in the stream (see dep_wait).
+template <typename K>
+static cudaError_t launch_k(K kern, int grid, int block, size_t smem, cudaStream_t st, bool pdl, const KArgs& a) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = pdl ? at : nullptr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
 cudaError_t launch_prep(const KArgs& a, cudaStream_t st) {
   const int n = a.scans ? a.nscans : 1;
   k_prep<<<n, NT_PREP, 0, st>>>(a);
@@ -1328,24 +1364,20 @@ cudaError_t launch_prep(const KArgs& a, cudaStream_t st) {
   }
 
 template <int TR, int NW>
-static cudaError_t run_tile(const KArgs& a, cudaStream_t st) {
-  k_tile<TR, NW><<<a.ntiles, NW * 32, Geo<TR, NW>::bytes, st>>>(a);
-  return cudaGetLastError();
+static cudaError_t run_tile(const KArgs& a, cudaStream_t st, bool pdl) {
+  return launch_k(k_tile<TR, NW>, a.ntiles, NW * 32, Geo<TR, NW>::bytes, st, pdl, a);
 }
 template <int TR, int NW>
-static cudaError_t run_tile_ccl(const KArgs& a, cudaStream_t st) {
-  k_tile_ccl<TR, NW><<<a.ntiles, NW * 32, Geo<TR, NW>::ccl_bytes, st>>>(a);
-  return cudaGetLastError();
+static cudaError_t run_tile_ccl(const KArgs& a, cudaStream_t st, bool pdl) {
+  return launch_k(k_tile_ccl<TR, NW>, a.ntiles, NW * 32, Geo<TR, NW>::ccl_bytes, st, pdl, a);
 }
 template <int TR, int NW>
-static cudaError_t run_merge(const KArgs& a, cudaStream_t st) {
-  k_merge<TR, NW><<<a.ntiles, nt_merge<TR, NW>(), 0, st>>>(a);
-  return cudaGetLastError();
+static cudaError_t run_merge(const KArgs& a, cudaStream_t st, bool pdl) {
+  return launch_k(k_merge<TR, NW>, a.ntiles, nt_merge<TR, NW>(), 0, st, pdl, a);
 }
 template <int TR, int NW>
-static cudaError_t run_flatten(const KArgs& a, cudaStream_t st) {
-  k_flatten<TR, NW><<<a.ntiles, NT_FLAT, FlatGeo<TR, NW>::bytes, st>>>(a);
-  return cudaGetLastError();
+static cudaError_t run_flatten(const KArgs& a, cudaStream_t st, bool pdl) {
+  return launch_k(k_flatten<TR, NW>, a.ntiles, NT_FLAT, FlatGeo<TR, NW>::bytes, st, pdl, a);
 }
 
 template <int TR, int NW>
@@ -1363,13 +1395,17 @@ static cudaError_t run_fused(const FusedArgs& f, cudaStream_t st) {
 
 cudaError_t launch_fused(int tile, const FusedArgs& f, cudaStream_t st) { LSG_DISPATCH(tile, run_fused, f, st) }
 
-cudaError_t launch_tile(int tile, const KArgs& a, cudaStream_t st) { LSG_DISPATCH(tile, run_tile, a, st) }
-cudaError_t launch_tile_ccl(int tile, const KArgs& a, cudaStream_t st) {
-  LSG_DISPATCH(tile, run_tile_ccl, a, st)
+cudaError_t launch_tile(int tile, const KArgs& a, cudaStream_t st, bool pdl) {
+  LSG_DISPATCH(tile, run_tile, a, st, pdl)
 }
-cudaError_t launch_merge(int tile, const KArgs& a, cudaStream_t st) { LSG_DISPATCH(tile, run_merge, a, st) }
-cudaError_t launch_flatten(int tile, const KArgs& a, cudaStream_t st) {
-  LSG_DISPATCH(tile, run_flatten, a, st)
+cudaError_t launch_tile_ccl(int tile, const KArgs& a, cudaStream_t st, bool pdl) {
+  LSG_DISPATCH(tile, run_tile_ccl, a, st, pdl)
+}
+cudaError_t launch_merge(int tile, const KArgs& a, cudaStream_t st, bool pdl) {
+  LSG_DISPATCH(tile, run_merge, a, st, pdl)
+}
+cudaError_t launch_flatten(int tile, const KArgs& a, cudaStream_t st, bool pdl) {
+  LSG_DISPATCH(tile, run_flatten, a, st, pdl)
 }
 
 }  // namespace lsg

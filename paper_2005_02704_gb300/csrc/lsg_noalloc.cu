@@ -90,8 +90,8 @@ extern "C" lsg_status lsg_segment_noalloc(const lsg_scan* scan, const lsg_params
   // everything else is fully written by the kernels before it is read.
   cudaError_t e = cudaMemsetAsync(a.err, 0, sizeof(int32_t), cs);
   if (e == cudaSuccess) e = lsg::launch_prep(a, cs);
-  if (e == cudaSuccess) e = lsg::launch_tile(LSG_TILE_16x240, a, cs);
-  if (e == cudaSuccess) e = lsg::launch_merge(LSG_TILE_16x240, a, cs);
-  if (e == cudaSuccess) e = lsg::launch_flatten(LSG_TILE_16x240, a, cs);
+  if (e == cudaSuccess) e = lsg::launch_tile(LSG_TILE_16x240, a, cs, true);
+  if (e == cudaSuccess) e = lsg::launch_merge(LSG_TILE_16x240, a, cs, true);
+  if (e == cudaSuccess) e = lsg::launch_flatten(LSG_TILE_16x240, a, cs, true);
   return e == cudaSuccess ? LSG_OK : LSG_E_CUDA;
 }
