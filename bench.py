@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--no-generator", action="store_true", help="skip timing the GPU scan generator")
     ap.add_argument("--no-spin", action="store_true", help="skip the streaming (per-packet) latency measurement")
     ap.add_argument("--no-single", action="store_true", help="skip the single-scan latency measurement")
+    ap.add_argument("--single-only", action="store_true",
+                    help="only the single-scan latency measurement (one JSON object; for profiling the per-call path)")
     ap.add_argument("--phased", action="store_true", help="force four phased launches (else the autotuner's choice)")
     ap.add_argument("--fused", action="store_true", help="force the single persistent launch")
     ap.add_argument("--grouped", action="store_true", help="force the grouped schedule")
@@ -479,6 +481,11 @@ def main():
     from paper_2005_02704_gb300 import replicas
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
+    if args.single_only:
+        if rank == 0:
+            print(json.dumps({"single_scans": single_scan_measurement(local, measured_hbm()[0],
+                                                                     reps=args.steps, warm=args.warmup)}), flush=True)
+        return
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     red = replicas.Reducer(world, device=torch.device("cuda", local))

@@ -712,10 +712,10 @@ lsg_status lsg_batch_plan(lsg_ctx* ctx, int32_t n, const lsg_scan* scans, const 
     Hs[b] = scans[b].cols > 0 ? scans[b].rings : 0;
   }
   if (tile == LSG_TILE_AUTO) tile = pick_tile(Hs.data(), Ws.data(), n, ctx->sms);
-  // bound on the tile table over every tile shape (at least 8 rows x 120 columns)
+  // bound on the tile table over every tile shape (at least 4 rows x 120 columns)
   size_t tiles_max = 0;
   for (int b = 0; b < n; ++b)
-    tiles_max += (size_t)(scans[b].rings / 8 + 1) * (Ws[b] / 120 + 1);
+    tiles_max += (size_t)(scans[b].rings / 4 + 1) * (Ws[b] / 120 + 1);
   // workspace, descriptors, tile table, fused schedule (scan + 3 items per tile) and counters
   const size_t bytes = ws_total + align_up(sizeof(ScanDesc) * n, 256) + sizeof(int32_t) * tiles_max +
                        sizeof(int2) * (n + 3 * tiles_max) + sizeof(int32_t) * (1 + 3 * (size_t)n);
@@ -869,13 +869,13 @@ struct lsg_spin {
 namespace {
 
 // Launches k_tile or k_merge over the tile columns at positions [q0, q1) of
-// the spin's column order (1, 2, .., last, 0).
-cudaError_t spin_launch(const lsg_spin* sp, bool merge, int q0, int q1, cudaStream_t cs) {
+// the spin's column order (1, 2, .., last, 0); pdl as for launch_tile.
+cudaError_t spin_launch(const lsg_spin* sp, bool merge, int q0, int q1, cudaStream_t cs, bool pdl = false) {
   if (q1 <= q0) return cudaSuccess;
   KArgs a = sp->a;
   a.tile_list = sp->d_cols + (size_t)q0 * a.one.tiles_r;
   a.ntiles = (q1 - q0) * a.one.tiles_r;
-  return merge ? launch_merge(sp->tile, a, cs) : launch_tile(sp->tile, a, cs);
+  return merge ? launch_merge(sp->tile, a, cs, pdl) : launch_tile(sp->tile, a, cs, pdl);
 }
 
 }  // namespace
@@ -976,15 +976,17 @@ lsg_status lsg_spin_finish(lsg_spin* sp, lsg_stream stream) {
   DeviceGuard g(sp->ctx->device);
   cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
   // the remaining tile columns and column 0 (the tail of the column
-  // order), then their joins, then labels: three launches
+  // order), then their joins, then labels: three launches, each non-empty
+  // (pushes never reach column 0 or its join), the last two as programmatic
+  // dependents of the one before
   cudaError_t e = spin_launch(sp, false, sp->done_to - 1, d.tiles_c, cs);
-  if (e == cudaSuccess) e = spin_launch(sp, true, sp->merged_to - 1, d.tiles_c, cs);
+  if (e == cudaSuccess) e = spin_launch(sp, true, sp->merged_to - 1, d.tiles_c, cs, true);
   sp->done_to = sp->merged_to = d.tiles_c;
   if (e == cudaSuccess) {
     KArgs a = sp->a;
     a.tile_list = nullptr;
     a.ntiles = d.tiles_r * d.tiles_c;
-    e = launch_flatten(sp->tile, a, cs);
+    e = launch_flatten(sp->tile, a, cs, true);
   }
   return cuda_status(e);
 }

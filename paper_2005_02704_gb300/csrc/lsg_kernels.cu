@@ -61,17 +61,18 @@ TileShape tile_shape(int tile) {
     case LSG_TILE_64x240: return {64, 240};
     case LSG_TILE_16x120: return {16, 120};
     case LSG_TILE_8x120: return {8, 120};
+    case LSG_TILE_4x120: return {4, 120};
     case LSG_TILE_16x240:
     default: return {16, 240};
   }
 }
 
 int pick_tile(const int* H, const int* Ws, int n, int sms) {
-  static const int order[5] = {LSG_TILE_32x120, LSG_TILE_32x240, LSG_TILE_16x240, LSG_TILE_16x120,
-                               LSG_TILE_8x120};
+  static const int order[6] = {LSG_TILE_32x120, LSG_TILE_32x240, LSG_TILE_16x240, LSG_TILE_16x120,
+                               LSG_TILE_8x120,  LSG_TILE_4x120};
   int best = order[0];
   long long best_n = -1;
-  for (int k = 0; k < 5; ++k) {
+  for (int k = 0; k < 6; ++k) {
     const TileShape ts = tile_shape(order[k]);
     long long nt = 0;
     for (int b = 0; b < n; ++b)
@@ -915,6 +916,8 @@ __device__ __forceinline__ void merge_body(const ScanDesc* d, int lt, int32_t* e
   const bool full_ring = L.wrap && L.c0 == 0 && L.cn == L.Ws;
   const size_t LP = root_pitch(L.Ws);
   const int lane = threadIdx.x & 31;
+  __shared__ uint64_t pairs_s[NTB / 32][96];  // each warp's distinct pairs (three per lane at most)
+  uint64_t* wk = pairs_s[threadIdx.x >> 5];
   // border vertices: the last row of the tile, then the last column above it
   const int nb = L.cn + L.rn - 1;
   for (int k0 = 0; k0 < nb; k0 += NTB) {  // trip count uniform over the block
@@ -957,15 +960,30 @@ __device__ __forceinline__ void merge_body(const ScanDesc* d, int lt, int32_t* e
       }
     }
     // a diagonal pair often repeats the next lane's down pair (bottom row)
-    // or right pair (right column): that lane's round joins it
+    // or right pair (right column): that lane's entry joins it
     const uint64_t nd = __shfl_down_sync(FULL, key[1], 1), nr = __shfl_down_sync(FULL, key[0], 1);
     if (lane < 31 && (key[2] == nd || key[2] == nr)) key[2] = NONE;
+    // the first lane of each group of equal pairs lists its pair, then the
+    // warp's list is deduplicated once more and joined one pair per lane
+    // (the unions of different pairs run side by side, not one edge kind
+    // after another)
+    int nk = 0;
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
       const unsigned same = __match_any_sync(FULL, key[e]);
-      if (key[e] != NONE && lane == __ffs(same) - 1)
-        union_g(parent, (int)(key[e] >> 32), (int)(key[e] & 0xffffffffu), limit, err);
+      const bool lead = key[e] != NONE && lane == __ffs(same) - 1;
+      const unsigned m = __ballot_sync(FULL, lead);
+      if (lead) wk[nk + __popc(m & ((1u << lane) - 1u))] = key[e];
+      nk += __popc(m);
     }
+    __syncwarp();
+    for (int k0 = 0; k0 < nk; k0 += 32) {
+      const uint64_t kk = k0 + lane < nk ? wk[k0 + lane] : NONE;
+      const unsigned same = __match_any_sync(FULL, kk);
+      if (kk != NONE && lane == __ffs(same) - 1)
+        union_g(parent, (int)(kk >> 32), (int)(kk & 0xffffffffu), limit, err);
+    }
+    __syncwarp();
   }
 }
 
@@ -1326,6 +1344,7 @@ cudaError_t prepare_kernels() {
   if ((e = set_attrs<64, 4>()) != cudaSuccess) return e;
   if ((e = set_attrs<16, 2>()) != cudaSuccess) return e;
   if ((e = set_attrs<8, 2>()) != cudaSuccess) return e;
+  if ((e = set_attrs<4, 2>()) != cudaSuccess) return e;
   return cudaSuccess;
 }
 
@@ -1360,6 +1379,7 @@ cudaError_t launch_prep(const KArgs& a, cudaStream_t st) {
     case LSG_TILE_64x240: return FN<64, 4>(__VA_ARGS__);  \
     case LSG_TILE_16x120: return FN<16, 2>(__VA_ARGS__);  \
     case LSG_TILE_8x120: return FN<8, 2>(__VA_ARGS__);    \
+    case LSG_TILE_4x120: return FN<4, 2>(__VA_ARGS__);    \
     default: return FN<16, 4>(__VA_ARGS__);               \
   }
 

@@ -160,7 +160,7 @@ class Server:
         # largest expected scan, so that serving allocates nothing
         H, W, s_ = max_shape
         Ws = lsg.ws_of(W, s_)
-        tiles = ((H + 7) // 8 + 1) * (Ws // 120 + 1)
+        tiles = ((H + 3) // 4 + 1) * (Ws // 120 + 1)  # the smallest tile shape: 4 x 120
         for c in self.ctxs:
             lsg.lsg_reserve(c.h, max_batch * lsg.scan_workspace_bytes(H, Ws), max_batch, 2 * max_batch * tiles)
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(lanes)]
