@@ -188,7 +188,7 @@ lsg_status lsg_destroy(lsg_ctx* ctx);
  * lsg_label_from_mask, lsg_batch_launch, lsg_spin_begin, and lsg_batch_plan
  * given LSG_TILE_AUTO).  LSG_TILE_AUTO (the default) lets each call pick from
  * its work: the first of 32x120, 32x240, 16x240, 16x120, 8x120, 4x120 that
- * gives at least two tiles per SM, else the one that gives the most tiles
+ * gives at least four tiles per SM, else the one that gives the most tiles
  * (small scans fill the GPU with small tiles of short row sweeps, large
  * batches keep the efficient ones). */
 lsg_status lsg_set_tile(lsg_ctx* ctx, int tile);

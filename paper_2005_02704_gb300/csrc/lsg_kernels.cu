@@ -77,7 +77,7 @@ int pick_tile(const int* H, const int* Ws, int n, int sms) {
     long long nt = 0;
     for (int b = 0; b < n; ++b)
       if (H[b] > 0 && Ws[b] > 0) nt += (long long)((H[b] + ts.rows - 1) / ts.rows) * ((Ws[b] + ts.cols - 1) / ts.cols);
-    if (nt >= 2LL * sms) return order[k];
+    if (nt >= 4LL * sms) return order[k];
     if (nt > best_n) {
       best_n = nt;
       best = order[k];
