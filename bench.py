@@ -51,6 +51,9 @@ FALLBACK_HBM_GBS = 6800.0
 PATH_BYTES_PER_POINT = 33.0
 # the fused tile kernel alone: 16 B read, 13 B written per point (s = 1)
 TILE_BYTES_PER_POINT = 29.0
+# range-only input at s = 1: the range (4 B) and the labels (4 B) per point,
+# a mesh byte and a normal (13 B) per vertex: 8 + 13/s
+RANGE_PATH_BYTES_PER_POINT = 21.0
 
 
 def parse():
@@ -67,6 +70,7 @@ def parse():
     ap.add_argument("--no-generator", action="store_true", help="skip timing the GPU scan generator")
     ap.add_argument("--no-spin", action="store_true", help="skip the streaming (per-packet) latency measurement")
     ap.add_argument("--no-single", action="store_true", help="skip the single-scan latency measurement")
+    ap.add_argument("--no-range-input", action="store_true", help="skip the range-only input measurement")
     ap.add_argument("--single-only", action="store_true",
                     help="only the single-scan latency measurement (one JSON object; for profiling the per-call path)")
     ap.add_argument("--phased", action="store_true", help="force four phased launches (else the autotuner's choice)")
@@ -608,6 +612,60 @@ def main():
     barrier()
     ms_e2e_serial = max_over_ranks(e0.elapsed_time(e1) / args.steps)
 
+    # ---- the same batch as ranges only (the sensor's own output form) -------
+    #     x,y,z decoded on the GPU from the ring elevation and column azimuth:
+    #     a quarter of the input bytes, on the device and over the host link
+    range_input = None
+    if not args.no_range_input:
+        dbr = batch.DeviceBatch(shapes, [seg_params(sp) for sp in specs], local, form="range")
+        for b, s_ in enumerate(scans):
+            dbr.set_scan(b, s_)
+        dbr.upload()
+        planr = dbr.plan(ctx, plan.tile)
+        planr.set_schedule(schedule)
+        for _ in range(max(args.warmup, 3)):
+            planr.run()
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            planr.run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms_r = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+        piper = dbr.pipeline(ctx, plan.tile, chunks=args.e2e_chunks, schedule=schedule)
+        for _ in range(max(args.warmup, 3)):
+            piper.step(stream)
+        regions_r = []
+        h2d_r = d2h_r = 0
+        with serve.no_gc_pauses():
+            for _ in range(3):
+                torch.cuda.synchronize()
+                barrier()
+                torch.cuda.synchronize()
+                e0.record(stream)
+                for _ in range(args.steps):
+                    h2d_r, d2h_r = piper.step(stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                barrier()
+                regions_r.append(max_over_ranks(e0.elapsed_time(e1) / args.steps))
+        if ctx.error() != lsg.LSG_OK:
+            raise RuntimeError("device error in the range-input measurement")
+        ms_er = statistics.median(regions_r)
+        piper.close()
+        planr.close()
+        del dbr
+        range_input = {"workload": "the same 512 scans, range float32 per point (x,y,z decoded on the GPU)",
+                       "value": pts_all / (ms_r / 1e3), "unit": UNIT, "ms_per_step": ms_r,
+                       "bytes_per_point": RANGE_PATH_BYTES_PER_POINT,
+                       "e2e": {"value": pts_all / (ms_er / 1e3), "unit": UNIT, "ms_per_step": ms_er,
+                               "ms_per_step_regions": regions_r, "h2d_bytes_per_step": h2d_r,
+                               "d2h_bytes_per_step": d2h_r,
+                               "path": f"HostPipeline, {args.e2e_chunks} chunks, 3 streams"}}
+
     # ---- plain per-scan path: one lsg_segment call per scan ----------------
     plain = None
     if not args.no_plain:
@@ -681,6 +739,8 @@ def main():
 
     if plain is not None:
         plain["path_roofline_frac"] = path_frac(plain["value"])
+    if range_input is not None:
+        range_input["path_roofline_frac"] = RANGE_PATH_BYTES_PER_POINT * range_input["value"] / 1e9 / peak
     if served is not None:
         for d in (served["batched"], served["serial_plain"], served["saturated"]["batched"],
                   served["saturated"]["serial_plain"]):
@@ -721,6 +781,7 @@ def main():
                     "serial_ms_per_step": ms_e2e_serial,
                     "serial_value": pts_all / (ms_e2e_serial / 1e3)},
             "batched_latency": batched_latency,
+            "range_input": range_input,
             "plain": plain,
             "single_scans": singles,
             "served": served,

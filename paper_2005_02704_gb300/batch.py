@@ -2,8 +2,8 @@
 served paths).
 
 All scans' inputs live in one device buffer (x,y,z,r float32, 16-byte
-aligned per scan) plus one buffer of elevations; all outputs in one buffer per
-kind.  ``lsg_scan`` / ``lsg_out`` descriptors point into them, so one
+aligned per scan, or, for range-only decoding, the ranges alone) plus one
+buffer of elevations; all outputs in one buffer per kind.  ``lsg_scan`` / ``lsg_out`` descriptors point into them, so one
 ``lsg_batch_plan`` covers the whole batch and replays stay valid as long as
 the buffers live.  A pinned host mirror of the inputs and of the labels and
 segment counts serves the end-to-end (host -> device -> host) path, which
@@ -40,9 +40,16 @@ class ScanShape:
 
 
 class DeviceBatch:
+    """form "xyzr": x,y,z,r float32 per point; "range": the range alone (the
+    library computes x,y,z from the ring elevation and the column azimuth)."""
+
     def __init__(self, shapes: Sequence[ScanShape], params: Sequence["lsg.Params"], device=0,
-                 pinned: bool = True):
+                 pinned: bool = True, form: str = "xyzr"):
         import torch
+        if form not in ("xyzr", "range"):
+            raise ValueError(f"unknown input form {form!r}")
+        self.form = form
+        self.in_width = 4 if form == "xyzr" else 1  # float32 values per input point
         self.torch = torch
         self.dev = torch.device("cuda", device) if isinstance(device, int) else device
         self.n = len(shapes)
@@ -59,13 +66,13 @@ class DeviceBatch:
         self.points = P
         self.vertices = V
         f32, i32, u8 = torch.float32, torch.int32, torch.uint8
-        self.d_xyzr = torch.empty((max(P, 1), 4), dtype=f32, device=self.dev)
+        self.d_in = torch.empty((max(P, 1), self.in_width), dtype=f32, device=self.dev)
         self.d_elev = torch.empty(max(E, 1), dtype=f32, device=self.dev)
         self.d_mb = torch.empty(max(V, 1), dtype=u8, device=self.dev)
         self.d_nrm = torch.empty((max(V, 1), 3), dtype=f32, device=self.dev)
         self.d_lab = torch.empty(max(P, 1), dtype=i32, device=self.dev)
         self.d_nseg = torch.zeros(max(self.n, 1), dtype=i32, device=self.dev)
-        self.h_xyzr = torch.empty((max(P, 1), 4), dtype=f32, pin_memory=pinned)
+        self.h_in = torch.empty((max(P, 1), self.in_width), dtype=f32, pin_memory=pinned)
         self.h_elev = torch.empty(max(E, 1), dtype=f32, pin_memory=pinned)
         self.h_lab = torch.empty(max(P, 1), dtype=i32, pin_memory=pinned)
         self.h_nseg = torch.empty(max(self.n, 1), dtype=i32, pin_memory=pinned)
@@ -78,7 +85,8 @@ class DeviceBatch:
         sh = self.shapes[b]
         assert scan.rings == sh.rings and scan.cols == sh.cols
         p0, p1 = self.pt_off[b], self.pt_off[b + 1]
-        self.h_xyzr[p0:p1].numpy()[:] = scan.xyzr.reshape(-1, 4)
+        src = scan.xyzr if self.form == "xyzr" else scan.range
+        self.h_in[p0:p1].numpy()[:] = src.reshape(-1, self.in_width)
         e0, e1 = self.e_off[b], self.e_off[b + 1]
         self.h_elev[e0:e1].numpy()[:] = scan.elev
         self.az0[b] = scan.az0
@@ -88,9 +96,9 @@ class DeviceBatch:
         """Host -> device copy of every input; returns the bytes copied."""
         torch = self.torch
         with torch.cuda.stream(stream) if stream is not None else _null():
-            self.d_xyzr.copy_(self.h_xyzr, non_blocking=non_blocking)
+            self.d_in.copy_(self.h_in, non_blocking=non_blocking)
             self.d_elev.copy_(self.h_elev, non_blocking=non_blocking)
-        return self.h_xyzr.numel() * 4 + self.h_elev.numel() * 4
+        return self.h_in.numel() * 4 + self.h_elev.numel() * 4
 
     def download(self, stream=None, non_blocking: bool = True) -> int:
         """Device -> host copy of the labels and segment counts; returns bytes."""
@@ -109,8 +117,9 @@ class DeviceBatch:
             sc.elevation = self.d_elev.data_ptr() + 4 * int(self.e_off[b]) if sh.rings else None
             sc.azimuth0 = float(self.az0[b])
             sc.azimuth_step = float(self.daz[b])
-            sc.xyzr = self.d_xyzr.data_ptr() + 16 * int(self.pt_off[b]) if sh.points else None
-            sc.range = None
+            ptr = self.d_in.data_ptr() + 4 * self.in_width * int(self.pt_off[b]) if sh.points else None
+            sc.xyzr = ptr if self.form == "xyzr" else None
+            sc.range = ptr if self.form == "range" else None
             out.append(sc)
         return out
 
@@ -149,7 +158,9 @@ class DeviceBatch:
         sh = self.shapes[b]
         p0, p1 = int(self.pt_off[b]), int(self.pt_off[b + 1])
         e0, e1 = int(self.e_off[b]), int(self.e_off[b + 1])
-        return self.d_elev[e0:e1], self.d_xyzr[p0:p1].view(sh.rings, sh.cols, 4)
+        if self.form == "range":
+            return self.d_elev[e0:e1], self.d_in[p0:p1].view(sh.rings, sh.cols)
+        return self.d_elev[e0:e1], self.d_in[p0:p1].view(sh.rings, sh.cols, 4)
 
 
 class HostPipeline:
@@ -203,7 +214,7 @@ class HostPipeline:
         for c, (b0, b1) in enumerate(self.ranges):
             p0, p1 = int(db.pt_off[b0]), int(db.pt_off[b1])
             with torch.cuda.stream(self.s_in):
-                db.d_xyzr[p0:p1].copy_(db.h_xyzr[p0:p1], non_blocking=True)
+                db.d_in[p0:p1].copy_(db.h_in[p0:p1], non_blocking=True)
                 self.ev_in[c].record(self.s_in)
             self.s_run.wait_event(self.ev_in[c])
             self.plans[c].run(stream=self.s_run)
@@ -212,7 +223,7 @@ class HostPipeline:
             with torch.cuda.stream(self.s_out):
                 db.h_lab[p0:p1].copy_(db.d_lab[p0:p1], non_blocking=True)
                 db.h_nseg[b0:b1].copy_(db.d_nseg[b0:b1], non_blocking=True)
-            h2d += (p1 - p0) * 16
+            h2d += (p1 - p0) * 4 * db.in_width
             d2h += (p1 - p0) * 4 + (b1 - b0) * 4
         self.ev_out.record(self.s_out)
         cur.wait_event(self.ev_out)

@@ -242,7 +242,8 @@ struct Geo {
   static constexpr size_t off_lp = 0;
   static constexpr size_t off_tb = ((ring_bytes > lp_bytes ? ring_bytes : lp_bytes) + 15) / 16 * 16;
   static constexpr size_t off_rows = off_tb + ((NV + 15) / 16) * 16;  // long long [HR] input row offsets
-  static constexpr size_t off_q = off_rows + ((sizeof(long long) * HR + 15) / 16) * 16;  // uint32 [NW][QCAP]
+  static constexpr size_t off_trig = off_rows + ((sizeof(long long) * HR + 15) / 16) * 16;  // float2 [HR] sin, cos
+  static constexpr size_t off_q = off_trig + ((sizeof(float2) * HR + 15) / 16) * 16;  // uint32 [NW][QCAP]
   // queue uint32 [NW][QCAP], then the run starts of every strip row uint16 [NW][TR][32]
   static constexpr size_t q_bytes = sizeof(uint32_t) * NW * QCAP + sizeof(uint16_t) * NW * TR * 32;
   static constexpr size_t bytes = off_q + q_bytes;
@@ -256,23 +257,21 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// Issue the asynchronous copy of one point into a ring slot (x,y,z,r input),
-// or store the decoded / absent value directly.  ro = offset of the input
-// row (ring order * W), or -1 when the row is outside the scan.
+// Issue the asynchronous copy of one point into a ring slot: x,y,z,r
+// (16 bytes), or the range alone (4 bytes, into the slot's r; the sweep
+// decodes x,y,z when it reads the slot).  ro = offset of the input row (ring
+// order * W), or -1 when the row is outside the scan: the slot then holds an
+// absent point (r = -1).
 __device__ __forceinline__ void fetch_point(float4* slot, const float4* __restrict__ xyzr,
-                                            const float* __restrict__ range, const float2* __restrict__ trig,
-                                            int i, long long ro, bool colok, unsigned coff, float sp, float cp) {
+                                            const float* __restrict__ range, long long ro, bool colok,
+                                            unsigned coff) {
   if (colok && ro >= 0) {
     const size_t o = (size_t)ro + coff;
-    if (xyzr) {
-      const unsigned dst = (unsigned)__cvta_generic_to_shared(slot);
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(slot);
+    if (xyzr)
       asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(xyzr + o) : "memory");
-    } else {
-      const float r = __ldg(range + o);
-      const float2 te = __ldg(trig + i);
-      const float rc = r * te.y;
-      *slot = make_float4(rc * cp, rc * sp, r * te.x, r);
-    }
+    else
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst + 12u), "l"(range + o) : "memory");
     return;
   }
   *slot = make_float4(0.f, 0.f, 0.f, -1.f);
@@ -419,10 +418,10 @@ __device__ __forceinline__ void tile_sweep(const ScanDesc* d, const Loc& L, unsi
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   float4* ring = reinterpret_cast<float4*>(smem + G::off_ring) + (size_t)w * (RING * 64) + lane;
   const long long* rows_s = reinterpret_cast<const long long*>(smem + G::off_rows);
+  const float2* trig_s = reinterpret_cast<const float2*>(smem + G::off_trig);
   uint8_t* tb = smem + G::off_tb;
   const float4* __restrict__ xyzr = d->xyzr;
   const float* __restrict__ range = d->range;
-  const float2* __restrict__ trig = d->trig;
   const float rmin = d->r_min, rmax = d->r_max;
 
   const int lcA = w * SO + 2 * lane - 2;  // tile column of the lane's first point
@@ -441,20 +440,14 @@ __device__ __forceinline__ void tile_sweep(const ScanDesc* d, const Loc& L, unsi
   const bool strip = lane >= 1 && lane <= SO / 2;  // holds two of the strip's columns
   const bool outA = strip && lcA < L.cn;            // first column is an output
   const bool outB = strip && lcA + 1 < L.cn;        // second column is an output
-  const int rbase = L.r0 - 1, nsteps = L.rn + 3;
+  const int nsteps = L.rn + 3;  // rows r0-1 .. r0+rn+1
   unsigned vout = (unsigned)L.r0 * (unsigned)L.Ws + (unsigned)(L.c0 + lcA);  // output vertex, tile row 0
 
   auto fetch = [&](int q, int k) {
     const long long ro = rows_s[k];
     float4* sl = ring + (q & (RING - 1)) * 64;
-    const int i = rbase + k;
-    if (XYZR) {
-      fetch_point(sl, xyzr, nullptr, nullptr, i, ro, okA, offA, 0.f, 1.f);
-      fetch_point(sl + 32, xyzr, nullptr, nullptr, i, ro, okB, offB, 0.f, 1.f);
-    } else {
-      fetch_point(sl, nullptr, range, trig, i, ro, okA, offA, spA, cpA);
-      fetch_point(sl + 32, nullptr, range, trig, i, ro, okB, offB, spB, cpB);
-    }
+    fetch_point(sl, XYZR ? xyzr : nullptr, range, ro, okA, offA);
+    fetch_point(sl + 32, XYZR ? xyzr : nullptr, range, ro, okB, offB);
   };
 #pragma unroll
   for (int q = 0; q < RING - 1; ++q) {
@@ -476,7 +469,13 @@ __device__ __forceinline__ void tile_sweep(const ScanDesc* d, const Loc& L, unsi
     // row hr has landed once at most RING-2 newer groups are pending
     cp_async_wait<RING - 2>();
     const int slot = hr & (RING - 1);
-    const float4 PA = ring[slot * 64], PB = ring[slot * 64 + 32];
+    float4 PA = ring[slot * 64], PB = ring[slot * 64 + 32];
+    if (!XYZR) {  // range-only input: x,y,z from the ring's elevation and the column's azimuth
+      const float2 te = trig_s[hr];
+      const float rcA = PA.w * te.y, rcB = PB.w * te.y;
+      PA = make_float4(rcA * cpA, rcA * spA, PA.w * te.x, PA.w);
+      PB = make_float4(rcB * cpB, rcB * spB, PB.w * te.x, PB.w);
+    }
     // refill the slot read one step ago with row hr+RING-1
     if (hr + RING - 1 < nsteps) fetch(hr + RING - 1, hr + RING - 1);
     cp_async_commit();
@@ -812,16 +811,21 @@ template <int TR, int NW>
 __device__ __forceinline__ void tile_body(const ScanDesc* d, int lt, unsigned char* smem, int32_t* err) {
   using G = Geo<TR, NW>;
   const Loc L = make_loc(d, lt, TR, G::TC);
-  // offsets of the input rows the tile reads (ring order applied once)
+  // offsets of the input rows the tile reads (ring order applied once) and,
+  // for range-only input, their elevations' sine and cosine
   long long* rows_s = reinterpret_cast<long long*>(smem + G::off_rows);
+  float2* trig_s = reinterpret_cast<float2*>(smem + G::off_trig);
   for (int k = threadIdx.x; k < L.rn + 3; k += G::NT) {
     const int i = L.r0 - 1 + k;
     long long ro = -1;
+    float2 te = make_float2(0.f, 1.f);
     if (i >= 0 && i < L.H) {
       const int row = __ldg(d->order + i);
       if ((unsigned)row < (unsigned)L.H) ro = (long long)row * L.W;
+      if (!d->xyzr) te = __ldg(d->trig + i);
     }
     rows_s[k] = ro;
+    trig_s[k] = te;
   }
   __syncthreads();
   const bool angle = d->pred == LSG_PRED_ANGLE;

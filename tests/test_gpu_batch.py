@@ -26,10 +26,10 @@ def params_of(spec):
                       jump_rel_v=spec.jump_rel_v, angle_rad=math.radians(spec.angle_deg))
 
 
-def make_batch(specs, scans):
+def make_batch(specs, scans, form="xyzr"):
     lsg, batch = mods()
     shapes = [batch.ScanShape(s.rings, s.cols, sp.subsample) for sp, s in zip(specs, scans)]
-    db = batch.DeviceBatch(shapes, [params_of(sp) for sp in specs], 0)
+    db = batch.DeviceBatch(shapes, [params_of(sp) for sp in specs], 0, form=form)
     for b, s in enumerate(scans):
         db.set_scan(b, s)
     db.upload()
@@ -78,6 +78,39 @@ def test_batch_equals_per_scan(ctx, tile, schedule):
         assert torch.equal(out.normals, nrm)
         assert torch.equal(out.labels, lab)
         assert torch.equal(out.nseg, nseg)
+    plan.close()
+
+
+@pytest.mark.parametrize("schedule", [1, 0, 2], ids=["fused", "phased", "grouped"])
+def test_range_input_batch_equals_per_scan(ctx, schedule):
+    """Range-only decoding in a batch (x,y,z from the ring elevation and the
+    column azimuth) equals the per-scan range-only path bit for bit, and the
+    chunked host pipeline over range inputs gives the same labels."""
+    lsg, _ = mods()
+    specs = mixed_specs(10, 5600)
+    scans = [lidarsim.make_scan(sp) for sp in specs]
+    db = make_batch(specs, scans, form="range")
+    plan = db.plan(ctx)
+    plan.set_schedule(schedule)
+    plan.run()
+    torch.cuda.synchronize()
+    assert ctx.error() == lsg.LSG_OK
+    for b, (sp, s) in enumerate(zip(specs, scans)):
+        mb, nrm, lab, nseg = db.view(b)
+        elev, rng = db.scan_inputs(b)
+        assert rng.shape == (s.rings, s.cols)
+        out = ctx.segment(elev, range_=rng, az0=s.az0, daz=s.daz, params=params_of(sp))
+        torch.cuda.synchronize()
+        assert torch.equal(out.meshbits, mb) and torch.equal(out.normals, nrm)
+        assert torch.equal(out.labels, lab) and torch.equal(out.nseg, nseg)
+    want_lab, want_nseg = db.d_lab.cpu().clone(), db.d_nseg.cpu().clone()
+    db.d_lab.fill_(-7)
+    pipe = db.pipeline(ctx, chunks=3, schedule=schedule)
+    h2d, d2h = pipe.step()
+    torch.cuda.synchronize()
+    assert h2d == db.points * 4 + db.h_elev.numel() * 4 and d2h == db.points * 4 + db.n * 4
+    assert torch.equal(db.h_lab, want_lab) and torch.equal(db.h_nseg, want_nseg)
+    pipe.close()
     plan.close()
 
 
