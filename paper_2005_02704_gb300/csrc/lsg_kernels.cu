@@ -44,6 +44,8 @@ namespace lsg {
 
 constexpr uint8_t B_R = LSG_BIT_R, B_D = LSG_BIT_D, B_G = LSG_BIT_G;
 constexpr uint8_t B_HR = LSG_BIT_HR, B_HD = LSG_BIT_HD, B_HG = LSG_BIT_HG;
+static_assert(B_HR == B_R << 3 && B_HD == B_D << 3 && B_HG == B_G << 3,
+              "a homogeneous bit is its edge bit three places up");
 constexpr uint8_t B_VALID = LSG_BIT_VALID, B_HASN = LSG_BIT_HASN;
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int SO = 60;  // output columns per warp strip (lanes 1..30, two columns each)
@@ -555,11 +557,13 @@ __device__ __forceinline__ void tile_sweep(const ScanDesc* d, const Loc& L, unsi
       homog2<ANGLE>(nx2, ny2, nz2, nRx, nRy, nRz, cos_t, ccx, ccy, ccz, hRA, hRB);
       homog2<ANGLE>(nx2, ny2, nz2, nx1, ny1, nz1, cos_t, ccx, ccy, ccz, hDA, hDB);
       homog2<ANGLE>(nx2, ny2, nz2, nGx, nGy, nGz, cos_t, ccx, ccy, ccz, hGA, hGB);
+      // an edge bit (R, D, G: bits 0-2 of each byte) moves up three places to
+      // its homogeneous bit (HR, HD, HG) where the predicate holds
+      const uint32_t hm = (hRA ? 1u : 0u) | (hDA ? 2u : 0u) | (hGA ? 4u : 0u) | (hRB ? 0x100u : 0u) |
+                          (hDB ? 0x200u : 0u) | (hGB ? 0x400u : 0u);
+      const uint32_t m2h = m2 | ((m2 & hm) << 3);
       const uint32_t m2A = m2 & 0xffu, m2B = m2 >> 8;
-      const uint32_t bA = m2A | (((m2A & B_R) && hRA) ? B_HR : 0u) | (((m2A & B_D) && hDA) ? B_HD : 0u) |
-                          (((m2A & B_G) && hGA) ? B_HG : 0u);
-      const uint32_t bB = m2B | (((m2B & B_R) && hRB) ? B_HR : 0u) | (((m2B & B_D) && hDB) ? B_HD : 0u) |
-                          (((m2B & B_G) && hGB) ? B_HG : 0u);
+      const uint32_t bA = m2h & 0xffu, bB = m2h >> 8;
       const int lr = hr - 3;
       if (lr < L.rn) {
         if (strip)
