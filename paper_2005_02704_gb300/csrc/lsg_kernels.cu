@@ -717,18 +717,19 @@ __device__ __forceinline__ void tile_components(const Loc& L, const uint8_t* __r
     }
     const uint32_t up = __shfl_up_sync(FULL, cur | (prev << 16), 1);
     const int upsB = __shfl_up_sync(FULL, psB, 1);
-    bool fDA = false, fGA = false, fDB = false, fGB = false;
-    if (act && lr > 0) {
-      const uint32_t pA = prev & 0xffu, pB = prev >> 8;
-      const uint32_t lB = (up >> 8) & 0xffu, lpB = up >> 24;  // left column: this row, previous row
-      // first column (its left: the previous lane's second column, or the
-      // previous strip's last column for lane 1, whose G edge is a C2 edge)
-      fDA = (pA & B_HD) && !((lpB & B_HD) && (lpB & B_HR) && (lB & B_HR));
-      fGA = lane > 1 && (lpB & B_HG) && !(((lpB & B_HD) && (lB & B_HR)) || ((lpB & B_HR) && (pA & B_HD)));
-      // second column (its left: the first)
-      fDB = (pB & B_HD) && !((pA & B_HD) && (pA & B_HR) && (bA & B_HR));
-      fGB = (pA & B_HG) && !(((pA & B_HD) && (bA & B_HR)) || ((pA & B_HR) && (pB & B_HD)));
-    }
+    // both columns at once, byte 0 the first and byte 1 the second: P the
+    // column's previous row, Lp and Lc its left neighbour's previous and this
+    // row (the first column's left: the previous lane's second column, or
+    // the previous strip's last column for lane 1, whose G edge is a C2
+    // edge; the second column's left: the first).  Shifted right by 3, 4 or
+    // 5 places, a byte's HR, HD or HG bit lands in the byte's bit 0.
+    const uint32_t P = prev;
+    const uint32_t Lp = (up >> 24) | ((prev & 0xffu) << 8), Lc = ((up >> 8) & 0xffu) | ((cur & 0xffu) << 8);
+    const uint32_t gate = (act && lr > 0) ? 0x0101u : 0u;
+    const uint32_t fD = (P >> 4) & ~((Lp >> 4) & (Lp >> 3) & (Lc >> 3)) & gate;
+    const uint32_t fG = (Lp >> 5) & ~(((Lp >> 4) & (Lc >> 3)) | ((Lp >> 3) & (P >> 4))) & gate &
+                        (lane > 1 ? 0x0101u : 0x0100u);
+    const bool fDA = fD & 1u, fGA = fG & 1u, fDB = (fD >> 8) & 1u, fGB = (fG >> 8) & 1u;
     queue_union(wq, qn, fDA, sA, psA);
     queue_union(wq, qn, fGA, sA, upsB);
     queue_union(wq, qn, fDB, sB, psB);
