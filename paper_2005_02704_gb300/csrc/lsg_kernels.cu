@@ -414,7 +414,7 @@ __device__ __forceinline__ float2 right_of(float2 v) {
 // d', gl' the edges from the row above): reversed spokes are folded into the
 // operand order.  A triangle (p, q, q') counts when its three edges exist.
 template <int TR, int NW, bool ANGLE, bool XYZR>
-__device__ __forceinline__ void tile_sweep(const ScanDesc* d, const Loc& L, unsigned char* smem) {
+__device__ __forceinline__ void tile_sweep(const ScanDesc* __restrict__ d, const Loc& L, unsigned char* smem) {
   using G = Geo<TR, NW>;
   constexpr int TC = G::TC;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -425,6 +425,10 @@ __device__ __forceinline__ void tile_sweep(const ScanDesc* d, const Loc& L, unsi
   const float4* __restrict__ xyzr = d->xyzr;
   const float* __restrict__ range = d->range;
   const float rmin = d->r_min, rmax = d->r_max;
+  // loop-invariant descriptor fields, read once
+  const float jump_h = d->jump_h, jump_v = d->jump_v, nsign = d->nsign;
+  const float cos_t = ANGLE ? d->cos_t : 0.f, ccx = ANGLE ? 0.f : d->comp_x, ccy = ANGLE ? 0.f : d->comp_y,
+              ccz = ANGLE ? 0.f : d->comp_z;
 
   const int lcA = w * SO + 2 * lane - 2;  // tile column of the lane's first point
   int jA = L.c0 + lcA, jB = jA + 1;       // scan columns
@@ -493,7 +497,7 @@ __device__ __forceinline__ void tile_sweep(const ScanDesc* d, const Loc& L, unsi
     // R edges of row k
     const float2 ex = sub2(qx, px), ey = sub2(qy, py), ez = sub2(qz, pz);
     const float2 le = len2(ex, ey, ez);
-    const float2 jh = make_float2(d->jump_h, d->jump_h), jv = make_float2(d->jump_v, d->jump_v);
+    const float2 jh = make_float2(jump_h, jump_h), jv = make_float2(jump_v, jump_v);
     bool cA, cB;
     jump_cut2(pr, qr, jh, cA, cB);
     const bool RA = vA && vB && !cA, RB = vB && vN && !cB;
@@ -531,7 +535,6 @@ __device__ __forceinline__ void tile_sweep(const ScanDesc* d, const Loc& L, unsi
     // is what a vertex out of range has: none of its triangles exists)
     const bool hA = q2.x >= FLT_MIN && q2.x < 3.0e38f;
     const bool hB = q2.y >= FLT_MIN && q2.y < 3.0e38f;
-    const float nsign = d->nsign;
     const float2 fn = make_float2(hA ? nsign * rsq_approx(q2.x) : QNAN, hB ? nsign * rsq_approx(q2.y) : QNAN);
     const float2 nx1 = mul2(sx, fn), ny1 = mul2(sy, fn), nz1 = mul2(sz, fn);
     const uint32_t m1 = (win & 0xffffu) | (hA ? (uint32_t)B_HASN : 0u) | (hB ? (uint32_t)B_HASN << 8 : 0u);
@@ -550,7 +553,6 @@ __device__ __forceinline__ void tile_sweep(const ScanDesc* d, const Loc& L, unsi
 
     // homogeneity mask and outputs of row k-2
     if (hr >= 3) {
-      const float cos_t = d->cos_t, ccx = d->comp_x, ccy = d->comp_y, ccz = d->comp_z;
       const float2 nRx = right_of(nx2), nRy = right_of(ny2), nRz = right_of(nz2);
       const float2 nGx = right_of(nx1), nGy = right_of(ny1), nGz = right_of(nz1);
       bool hRA, hRB, hDA, hDB, hGA, hGB;
