@@ -323,6 +323,16 @@ lsg_status lsg_plan_destroy(lsg_plan* plan);
  * device).  LSG_OK when no device-side error was recorded. */
 lsg_status lsg_get_error(lsg_ctx* ctx);
 
+/* Self-test of failure detection, without a fault: a kernel runs the
+ * persistent schedule's bounded wait on a device counter that nothing
+ * increments, gives up after about 4096 polls (about a millisecond) and
+ * records a timeout in the context's error word.  Returns LSG_OK when
+ * lsg_get_error then reports LSG_E_TIMEOUT (which it clears, so the context
+ * stays usable), LSG_E_DEVICE when it reports something else or nothing, and
+ * a CUDA or allocation status on failure.  Synchronises the device; any
+ * error word recorded before the call is read and cleared with it. */
+lsg_status lsg_selftest_wait_timeout(lsg_ctx* ctx);
+
 /*
  * Per-segment statistics and small-segment removal: the optional
  * post-processing of Sec. 2 (last paragraph), which eliminates segments with

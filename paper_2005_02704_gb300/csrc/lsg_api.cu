@@ -357,6 +357,22 @@ lsg_status lsg_label_from_mask(lsg_ctx* ctx, int32_t H, int32_t W, int32_t s, in
   return cuda_status(e);
 }
 
+lsg_status lsg_selftest_wait_timeout(lsg_ctx* ctx) {
+  if (!ctx) return LSG_E_ARG;
+  DeviceGuard g(ctx->device);
+  int32_t* cnt = nullptr;
+  cudaError_t e = cudaMalloc(&cnt, sizeof(int32_t));
+  if (e != cudaSuccess) return cuda_status(e);
+  e = cudaMemset(cnt, 0, sizeof(int32_t));
+  if (e == cudaSuccess) e = launch_wait_probe(cnt, ctx->d_err, 4096u, nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cudaFree(cnt);
+  if (e != cudaSuccess) return cuda_status(e);
+  const lsg_status st = lsg_get_error(ctx);
+  if (st == LSG_E_TIMEOUT) return LSG_OK;
+  return st == LSG_OK ? LSG_E_DEVICE : st;
+}
+
 lsg_status lsg_get_error(lsg_ctx* ctx) {
   if (!ctx) return LSG_E_ARG;
   DeviceGuard g(ctx->device);

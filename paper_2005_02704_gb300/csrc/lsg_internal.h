@@ -90,6 +90,9 @@ cudaError_t launch_tile_ccl(int tile, const KArgs& a, cudaStream_t st, bool pdl 
 cudaError_t launch_merge(int tile, const KArgs& a, cudaStream_t st, bool pdl = false);
 cudaError_t launch_flatten(int tile, const KArgs& a, cudaStream_t st, bool pdl = false);
 cudaError_t launch_fused(int tile, const FusedArgs& f, cudaStream_t st);
+// The persistent schedule's bounded wait on a counter nothing increments
+// (cnt: a zeroed device int), giving up after `limit` polls.
+cudaError_t launch_wait_probe(const int32_t* cnt, int32_t* err, unsigned limit, cudaStream_t st);
 cudaError_t prepare_kernels();  // one-time function attributes
 
 }  // namespace lsg

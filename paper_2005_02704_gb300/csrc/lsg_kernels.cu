@@ -1267,16 +1267,23 @@ __global__ void __launch_bounds__(NT_FLAT, (flat_min_blocks<TR, NW>())) k_flatte
 // ---------------------------------------------------------------------------
 // Waits (one thread) until *cnt reaches need; gives up after about a second,
 // recording a timeout in the error word instead of hanging.
-__device__ __forceinline__ void wait_count(const int32_t* cnt, int need, int32_t* err) {
+__device__ __forceinline__ void wait_count(const int32_t* cnt, int need, int32_t* err,
+                                           unsigned limit = 1u << 23) {
   for (unsigned it = 0;; ++it) {
     if (*reinterpret_cast<const volatile int32_t*>(cnt) >= need) break;
-    if (it > (1u << 23)) {
+    if (it > limit) {
       atomicOr(err, DERR_TIMEOUT);
       break;
     }
     __nanosleep(128);
   }
   __threadfence();
+}
+
+// Self-test of the bounded wait: one thread waits for a counter that nothing
+// increments, gives up after `limit` polls and flags the timeout.
+__global__ void k_wait_probe(const int32_t* cnt, int32_t* err, unsigned limit) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) wait_count(cnt, 1, err, limit);
 }
 
 template <int TR, int NW>
@@ -1374,6 +1381,11 @@ static cudaError_t launch_k(K kern, int grid, int block, size_t smem, cudaStream
   cfg.attrs = pdl ? at : nullptr;
   cfg.numAttrs = pdl ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
+cudaError_t launch_wait_probe(const int32_t* cnt, int32_t* err, unsigned limit, cudaStream_t st) {
+  k_wait_probe<<<1, 32, 0, st>>>(cnt, err, limit);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_prep(const KArgs& a, cudaStream_t st) {

@@ -103,6 +103,7 @@ def load(build: bool = True):
             "lsg_plan_phase_times": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float)]),
             "lsg_plan_destroy": (ctypes.c_int, [_P]),
             "lsg_get_error": (ctypes.c_int, [_P]),
+            "lsg_selftest_wait_timeout": (ctypes.c_int, [_P]),
             "lsg_segment_stats": (ctypes.c_int, [_P, I32, I32, I32, I32, _P, _P, _P, _P, _P, _P, _P]),
             "lsg_segment_noalloc": (ctypes.c_int, [ctypes.POINTER(lsg_scan), ctypes.POINTER(lsg_params),
                                                    ctypes.POINTER(lsg_out), _P]),

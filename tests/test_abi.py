@@ -63,6 +63,7 @@ def test_null_arguments_are_rejected_without_a_device():
     assert lib.lsg_batch_run(None, None) == lsg.LSG_E_ARG
     assert lib.lsg_get_error(None) == lsg.LSG_E_ARG
     assert lib.lsg_plan_launches(None) == -1 and lib.lsg_plan_tile(None) == -1
+    assert lib.lsg_selftest_wait_timeout(None) == lsg.LSG_E_ARG
     h = ctypes.c_void_p()
     # no CUDA device on this side: creating a context must fail cleanly
     import torch
