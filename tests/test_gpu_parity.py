@@ -150,6 +150,21 @@ def test_ragged_shapes(ctx, H, W, s, wrap, tile):
     full_check(ctx, scan, params_of(spec, wrap=wrap), tile=lsg.TILES[tile])
 
 
+RANGE_RAGGED = [(17, 257, 3, 0, "4x120"), (9, 131, 1, 1, "8x120"), (33, 361, 2, 1, "16x120"),
+                (5, 1030, 1, 1, "32x240"), (35, 121, 1, 0, "32x120")]
+
+
+@pytest.mark.parametrize("H,W,s,wrap,tile", RANGE_RAGGED)
+def test_range_only_ragged_shapes(ctx, H, W, s, wrap, tile):
+    """Range-only decode (4-byte asynchronous copies, x,y,z formed when a
+    row is read) on ragged shapes, small tiles and both seam modes."""
+    lsg = lsg_mod()
+    spec = lidarsim.ring64(seed=4400 + H * 31 + W, cols=W, rings=max(H, 2), subsample=s, angle_deg=10.0)
+    spec = replace(spec, elev_deg=lidarsim.elev_horizon_dense(max(H, 2))[:H], p_drop=0.1)
+    scan = lidarsim.make_scan(spec)
+    full_check(ctx, scan, params_of(spec, wrap=wrap), range_only=True, tile=lsg.TILES[tile])
+
+
 def test_edge_cases(ctx):
     lsg = lsg_mod()
     dev = torch.device("cuda", 0)
