@@ -244,6 +244,44 @@ def test_depth_jump_cuts_only_across_the_step():
     assert not (vcut[:-1, 3] & O.BIT_G).any() and (vcut[:-1, 3] & O.BIT_D).all()
 
 
+def _pair_cut(r_p, r_q, tau):
+    """Is the R edge of a 1 x 2 ring (ranges r_p, r_q) cut at threshold tau?
+    And the D and G edges of a 2 x 2 grid whose top row is r_p and bottom row
+    r_q, with the same threshold as jump_rel_v?"""
+    rs = np.array([[r_p, r_q]], np.float32)
+    mh = O.mesh(rs, np.ones((1, 2), np.uint8), 1, 0, tau, np.inf)
+    rv = np.array([[r_p, r_p], [r_q, r_q]], np.float32)
+    mv = O.mesh(rv, np.ones((2, 2), np.uint8), 1, 0, np.inf, tau)
+    return (not (mh[0, 0] & O.BIT_R), not (mv[0, 0] & O.BIT_D), not (mv[0, 0] & O.BIT_G))
+
+
+def test_depth_jump_threshold_scales_with_the_nearer_range():
+    # cut <=> |r_p - r_q| > tau * min(r_p, r_q): ranges 10 and 12 differ by
+    # exactly 2; tau = 0.18 gives 1.8 on the nearer range (cut) but 2.16 on
+    # the farther one (kept), in either order of the two points
+    assert _pair_cut(10.0, 12.0, 0.18) == (True, True, True)
+    assert _pair_cut(12.0, 10.0, 0.18) == (True, True, True)
+    # tau = 0.21: 2.1 on the nearer range, kept
+    assert _pair_cut(10.0, 12.0, 0.21) == (False, False, False)
+
+
+def test_depth_jump_at_the_threshold_is_kept():
+    # strict '>': ranges 2 and 3 with tau = 0.5 give |dr| = 1 = tau * 2
+    # exactly (binary32), which does not cut; a hair less cuts
+    assert float(np.float32(0.5) * np.float32(2.0)) == 1.0
+    assert _pair_cut(2.0, 3.0, 0.5) == (False, False, False)
+    assert _pair_cut(3.0, 2.0, 0.5) == (False, False, False)
+    assert _pair_cut(2.0, 3.0, float(np.nextafter(np.float32(0.5), np.float32(0)))) == (True, True, True)
+
+
+def test_range_validity_bounds():
+    # Sec. 2 "within range of the Lidar": r_min < r <= r_max; r at r_max is
+    # in range, r at r_min is not
+    r = np.array([[1.0, 2.0, 4.5, 4.50001]], np.float32)
+    _, _, _, valid = O.decode(np.zeros(1, np.float32), 0.0, 0.1, None, r, 1.0, 4.5)
+    assert valid.tolist() == [[0, 1, 1, 0]]
+
+
 # --------------------------------------------------------------------------
 # step 3: normals
 # --------------------------------------------------------------------------
@@ -372,6 +410,33 @@ def test_angle_predicate_threshold():
             assert m == pytest.approx(-sgn * eps, abs=1e-12)
 
 
+def test_predicates_are_strict_at_equality():
+    # Algorithm 1 compares with a strict '<'.  Angle form: equal normals make
+    # an angle of exactly 0, so a threshold of 0 admits nothing; orthogonal
+    # axes make atan2(1, 0) = pi/2 exactly, so pi/2 admits nothing either
+    assert O.angle([0, 0, 1], [0, 0, 1]) == 0.0
+    h, m = _two_vertex_mask([0, 0, 1], [0, 0, 1], O.PRED_ANGLE, 0.0)
+    assert not h and m == 0.0
+    h, _ = _two_vertex_mask([0, 0, 1], [0, 0, 1], O.PRED_ANGLE, 1e-12)
+    assert h
+    assert O.angle([1, 0, 0], [0, 1, 0]) == math.pi / 2
+    h, _ = _two_vertex_mask([1, 0, 0], [0, 1, 0], O.PRED_ANGLE, math.pi / 2)
+    assert not h
+    # component form: a difference of exactly the threshold (dyadic values,
+    # exact in binary64) on any one axis fails; the other axes are far inside
+    n0 = [0.0, 0.0, 1.0]
+    n1 = [0.25, 0.125, 0.75]
+    d = [0.25, 0.125, 0.25]
+    for axis in range(3):
+        comp = [1.0, 1.0, 1.0]
+        comp[axis] = d[axis]
+        h, m = _two_vertex_mask(n0, n1, O.PRED_COMPONENT, 0.0, comp)
+        assert not h and m == 0.0
+        comp[axis] = d[axis] * (1 + 2 ** -40)
+        h, _ = _two_vertex_mask(n0, n1, O.PRED_COMPONENT, 0.0, comp)
+        assert h
+
+
 def test_component_predicate_is_strict_componentwise():
     # (Algorithm 1): |di| < I, |dj| < J, |dk| < K
     base = unit([0.3, 0.2, 1.0])
@@ -437,6 +502,19 @@ def test_backfill_hand_worked_ring():
     vl = np.array([g["vlabel"]], np.int32)
     assert list(O.backfill(valid, vl, W, s, 0)[0]) == g["nowrap"]
     assert list(O.backfill(valid, vl, W, s, 1)[0]) == g["wrap"]
+
+
+@pytest.mark.parametrize("case", ["s2", "s4", "s4u", "s3w"])
+def test_backfill_ties_between_different_labels(case):
+    # Sec. 2, last paragraph: nearest labelled point along the sweep; equal
+    # distances go to the earlier sampled column (fixture worked by hand)
+    g = _read_golden("backfill_ties.txt")
+    W, s = g[case + "_W"][0], g[case + "_s"][0]
+    valid = np.array([g[case + "_valid"]], np.uint8)
+    vl = np.array([g[case + "_vlabel"]], np.int32)
+    assert len(g[case + "_valid"]) == W and vl.shape[1] == O.ws_of(W, s)
+    assert list(O.backfill(valid, vl, W, s, 0)[0]) == g[case + "_nowrap"]
+    assert list(O.backfill(valid, vl, W, s, 1)[0]) == g[case + "_wrap"]
 
 
 # --------------------------------------------------------------------------
