@@ -71,6 +71,7 @@ def parse():
     ap.add_argument("--no-spin", action="store_true", help="skip the streaming (per-packet) latency measurement")
     ap.add_argument("--no-single", action="store_true", help="skip the single-scan latency measurement")
     ap.add_argument("--no-range-input", action="store_true", help="skip the range-only input measurement")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the Table-2 accuracy protocol")
     ap.add_argument("--single-only", action="store_true",
                     help="only the single-scan latency measurement (one JSON object; for profiling the per-call path)")
     ap.add_argument("--phased", action="store_true", help="force four phased launches (else the autotuner's choice)")
@@ -216,6 +217,13 @@ def oracle_rate(specs, scans, budget_points, threads):
     return pts / dt, pts, len(idx), dt
 
 
+def workload_config(n_scans, points, world):
+    """The workload both arms measure (identical dicts on both arms)."""
+    return {"workload": WORKLOAD, "scans_per_gpu": n_scans, "points_per_gpu": points,
+            "l2": "inputs larger than L2 (x,y,z,r %.2f GB per GPU > 129 MB), no flush" % (points * 16 / 1e9),
+            "parallelism": f"replicas x{world}"}
+
+
 def host_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -234,23 +242,24 @@ def run_reference(args):
     oracle.build()
     specs, scans = batch_data(args.scans, 0)
     cores = host_cores()
-    budget = 4.0e6  # points per step: a bounded sample, a few seconds of host work
+    points = sum(s.points for s in scans)
+    # each step is the whole batch, one scan per thread on every host core
+    # (about a second of host work per step at 16 cores)
     for _ in range(args.warmup):
-        oracle_rate(specs, scans, budget, cores)
-    rates, pts_total, t_total = [], 0, 0.0
+        oracle_rate(specs, scans, float(points), cores)
+    pts_total, t_total = 0, 0.0
     for _ in range(args.steps):
-        r, pts, ns, dt = oracle_rate(specs, scans, budget, cores)
-        rates.append(r)
+        r, pts, ns, dt = oracle_rate(specs, scans, float(points), cores)
         pts_total += pts
         t_total += dt
     value = pts_total / t_total
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t_total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "scans": args.scans},
+            "data": "synthetic", "config": workload_config(len(scans), points, args.gpus),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"every {max(1, int(math.ceil(sum(s.points for s in scans) / budget)))}th "
-                                       f"scan of the batch per step (~{budget / 1e6:.0f} M points)"},
+                             "sample": f"the whole batch ({len(scans)} scans, {points / 1e6:.1f} M points) per step, "
+                                       f"one scan per thread on {cores} threads"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -552,6 +561,24 @@ def main():
     lat = sorted(a.elapsed_time(b) for a, b in lat_ev)
     batched_latency = {"p50_ms": pct(lat, 0.5), "p99_ms": pct(lat, 0.99), "passes": len(lat)}
 
+    # ---- every schedule of the same plan and tile shape --------------------
+    #      (K replays each, events on the launching stream)
+    sched_ms = {}
+    for sch, nm in ((0, "phased"), (1, "fused"), (2, "grouped")):
+        plan.set_schedule(sch)
+        for _ in range(3):
+            plan.run()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            plan.run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sched_ms[nm] = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+    plan.set_schedule(schedule)
+    if ctx.error() != lsg.LSG_OK:
+        raise RuntimeError("device error while timing the schedules")
+
     # ---- per-phase device times (events recorded inside the graph) ---------
     # (the grouped schedule overlaps its kernels, so its per-kernel times are
     # taken from the phased capture of the same plan)
@@ -713,6 +740,15 @@ def main():
                                           sum_over_ranks)
     if not args.no_serve:
         served = serve_measurement(args, local, world, max_over_ranks, sum_over_ranks)
+    accuracy = None
+    if not args.no_accuracy and rank == 0:
+        from paper_2005_02704_gb300 import evaluate
+        rows = evaluate.table2(n_scenes=8)
+        accuracy = {"protocol": "Sec. 3 edge-based precision / recall / F1, dilation radius 1, component predicate "
+                                "I=J=K=0.2, 8 synthetic Velodyne-32E-like scenes (32 x 1800), ground truth = "
+                                "primitive face per ray",
+                    "rows": [{"interval": s_, "precision": p_, "recall": r_, "f1": f_} for s_, p_, r_, f_ in rows],
+                    "paper_f1": {"5": 0.7406, "10": 0.7147, "15": 0.6910}}
 
     # ---- roofline of the dominant kernel ---------------------------------
     # the fused plan runs the whole pass in one persistent launch (k_fused),
@@ -763,12 +799,10 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "scans_per_gpu": db.n, "points_per_gpu": db.points,
-                       "tile": tile_name, "schedule": SCHEDULES[schedule],
-                       "autotune_ms": tuned[1] if tuned else None,
-                       "l2": "inputs larger than L2 (x,y,z,r %.2f GB per GPU > 129 MB), no flush" % (
-                           db.points * 16 / 1e9),
-                       "parallelism": f"replicas x{world}"},
+            "config": workload_config(db.n, db.points, world),
+            "plan": {"tile": tile_name, "schedule": SCHEDULES[schedule],
+                     "autotune_ms": tuned[1] if tuned else None, "launches_per_pass": launches_per_pass},
+            "schedule_ms": sched_ms,
             "roofline": roof,
             "path_roofline": {"bound": "hbm", "achieved": path_achieved, "peak": peak, "unit": "GB/s",
                               "frac": path_achieved / peak, "bytes_per_point": PATH_BYTES_PER_POINT},
@@ -788,6 +822,7 @@ def main():
             "generator": generator,
             "streaming": spin,
             "paper_table1": PAPER_TABLE1,
+            "accuracy": accuracy,
             "scans_per_s": db.n * world / (ms_step / 1e3),
             "gpu_launches": launches_per_pass * args.steps,
             "clocks": clk,

@@ -408,16 +408,28 @@ lsg_status lsg_spin_destroy(lsg_spin* spin);
  *   LSG_NOALLOC_MAX_VERTICES (nothing is launched), LSG_E_ARG / LSG_E_SHAPE
  *   as lsg_segment for bad arguments, LSG_E_CUDA if a launch fails.
  *
- * The first call on each device looks up the array's device address (make
- * it from a thread where that device is current).  Every call shares the one
- * array and leaves its contents behind, so calls whose work overlaps on the
- * GPU (different streams, or different host threads, without ordering
- * between them) race and corrupt each other's results: order them on one
- * stream.  Device-side flags (a NaN elevation) are not reported by this
- * entry point.
+ * Every call looks up the array's device address on the current device (a
+ * host-side lookup; the first call on a device also sets the kernels'
+ * shared-memory attributes).  Every call shares the one array and leaves its
+ * contents behind, so calls whose work overlaps on the GPU (different
+ * streams, or different host threads, without ordering between them) race
+ * and corrupt each other's results: order them on one stream.  Device-side
+ * flags (a NaN elevation) are not returned by this call; it clears them at
+ * its start, and lsg_noalloc_get_error reads them.
  */
 lsg_status lsg_segment_noalloc(const lsg_scan* scan, const lsg_params* params, const lsg_out* out,
                                lsg_stream stream);
+
+/*
+ * The device flags of the allocation-free passes (the paper has no
+ * counterpart).  Waits for `stream`, reads the flags the last
+ * lsg_segment_noalloc call on the current device raised, clears them, and
+ * returns LSG_OK (none), LSG_E_DEVICE (bad input seen on the device, e.g. a
+ * NaN elevation, whose outputs are then unspecified), LSG_E_TIMEOUT (a
+ * bounded union-find loop ran out) or LSG_E_CUDA.  Allocates nothing; call it
+ * on the stream of the pass it checks.
+ */
+lsg_status lsg_noalloc_get_error(lsg_stream stream);
 
 #ifdef __cplusplus
 }

@@ -101,6 +101,17 @@ int pick_tile(const int* H, const int* Ws, int n, int sms) {
 __device__ __forceinline__ void dep_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
 __device__ __forceinline__ void dep_release() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
 
+// Load of data another kernel wrote (CO = false: the read-only data path,
+// for data that does not change while the kernel runs) or that an earlier
+// work item of the same persistent launch wrote (CO = true: ld.global.cg,
+// which reads L2, where the producer's writes are visible once its release
+// count has been observed).
+template <bool CO, typename T>
+__device__ __forceinline__ T ld_in(const T* p) {
+  if constexpr (CO) return __ldcg(p);
+  else return __ldg(p);
+}
+
 __device__ __forceinline__ bool in_range(float r, float rmin, float rmax) {
   return rmin < r && r <= rmax;
 }
@@ -814,7 +825,7 @@ __device__ __forceinline__ void tile_cross_and_roots(const Loc& L, const uint8_t
 
 // One tile of one scan: decode + mesh + normals + edge mask + tile
 // components (smem: Geo<TR,NW>::bytes of dynamic shared memory).
-template <int TR, int NW>
+template <int TR, int NW, bool CO = false>
 __device__ __forceinline__ void tile_body(const ScanDesc* d, int lt, unsigned char* smem, int32_t* err) {
   using G = Geo<TR, NW>;
   const Loc L = make_loc(d, lt, TR, G::TC);
@@ -827,9 +838,9 @@ __device__ __forceinline__ void tile_body(const ScanDesc* d, int lt, unsigned ch
     long long ro = -1;
     float2 te = make_float2(0.f, 1.f);
     if (i >= 0 && i < L.H) {
-      const int row = __ldg(d->order + i);
+      const int row = ld_in<CO>(d->order + i);
       if ((unsigned)row < (unsigned)L.H) ro = (long long)row * L.W;
-      if (!d->xyzr) te = __ldg(d->trig + i);
+      if (!d->xyzr) te = ld_in<CO>(d->trig + i);
     }
     rows_s[k] = ro;
     trig_s[k] = te;
@@ -892,9 +903,9 @@ __global__ void __launch_bounds__(NW * 32) k_tile_ccl(const __grid_constant__ KA
 // global roots
 // ---------------------------------------------------------------------------
 // Scan-local index of the tile-local root of vertex (i, j).
-template <int TR, int TC>
-__device__ __forceinline__ int tile_root(const uint16_t* __restrict__ lroot, int Ws, int i, int j) {
-  const int r = lroot[(size_t)i * root_pitch(Ws) + j];
+template <int TR, int TC, bool CO = false>
+__device__ __forceinline__ int tile_root(const uint16_t* lroot, int Ws, int i, int j) {
+  const int r = ld_in<CO>(lroot + (size_t)i * root_pitch(Ws) + j);
   const int rr = r / TC, rc = r - (r / TC) * TC;
   return ((i / TR) * TR + rr) * Ws + (j / TC) * TC + rc;
 }
@@ -914,14 +925,14 @@ __host__ __device__ constexpr int nt_merge() {
 // homogeneous edges join, as (smaller, larger) scan-local indices.  Along a
 // border most pairs repeat (a component crossing it joins the same two tile
 // roots at every column), so each warp issues every distinct pair once.
-template <int TR, int NW, int NTB>
+template <int TR, int NW, int NTB, bool CO = false>
 __device__ __forceinline__ void merge_body(const ScanDesc* d, int lt, int32_t* err) {
   static_assert(NTB % 32 == 0, "whole warps");
   constexpr int TC = NW * SO;
   constexpr uint64_t NONE = ~0ull;
   const Loc L = make_loc(d, lt, TR, TC);
-  const uint8_t* __restrict__ mb = d->mb;
-  const uint16_t* __restrict__ lroot = d->lroot;
+  const uint8_t* mb = d->mb;
+  const uint16_t* lroot = d->lroot;
   int32_t* parent = d->parent;
   const int limit = L.H * L.Ws + 1;
   const bool full_ring = L.wrap && L.c0 == 0 && L.cn == L.Ws;
@@ -944,7 +955,7 @@ __device__ __forceinline__ void merge_body(const ScanDesc* d, int lt, int32_t* e
         lc = L.cn - 1;
       }
       const int i = L.r0 + lr, j = L.c0 + lc;
-      const uint8_t bits = mb[(size_t)i * L.Ws + j];
+      const uint8_t bits = ld_in<CO>(mb + (size_t)i * L.Ws + j);
       // bits pointing off the grid (possible in a caller-given mask) are ignored
       const bool has_right = (j + 1 < L.Ws) || L.wrap;
       const bool has_down = i + 1 < L.H;
@@ -954,18 +965,18 @@ __device__ __forceinline__ void merge_body(const ScanDesc* d, int lt, int32_t* e
       const bool hr_out = (bits & B_HR) && has_right && !jn_in;
       const bool hd_out = (bits & B_HD) && has_down && !down_in;
       const bool hg_out = (bits & B_HG) && has_down && has_right && !(down_in && jn_in);
-      if ((hr_out || hd_out || hg_out) && lroot[(size_t)i * LP + j] != NO_ROOT) {
-        const int rp = tile_root<TR, TC>(lroot, L.Ws, i, j);
+      if ((hr_out || hd_out || hg_out) && ld_in<CO>(lroot + (size_t)i * LP + j) != NO_ROOT) {
+        const int rp = tile_root<TR, TC, CO>(lroot, L.Ws, i, j);
         auto pair = [rp](int rq) {
           const uint32_t lo = (uint32_t)min(rp, rq), hi = (uint32_t)max(rp, rq);
           return ((uint64_t)lo << 32) | hi;
         };
-        if (hr_out && lroot[(size_t)i * LP + jn] != NO_ROOT)
-          key[0] = pair(tile_root<TR, TC>(lroot, L.Ws, i, jn));
-        if (hd_out && lroot[(size_t)(i + 1) * LP + j] != NO_ROOT)
-          key[1] = pair(tile_root<TR, TC>(lroot, L.Ws, i + 1, j));
-        if (hg_out && lroot[(size_t)(i + 1) * LP + jn] != NO_ROOT)
-          key[2] = pair(tile_root<TR, TC>(lroot, L.Ws, i + 1, jn));
+        if (hr_out && ld_in<CO>(lroot + (size_t)i * LP + jn) != NO_ROOT)
+          key[0] = pair(tile_root<TR, TC, CO>(lroot, L.Ws, i, jn));
+        if (hd_out && ld_in<CO>(lroot + (size_t)(i + 1) * LP + j) != NO_ROOT)
+          key[1] = pair(tile_root<TR, TC, CO>(lroot, L.Ws, i + 1, j));
+        if (hg_out && ld_in<CO>(lroot + (size_t)(i + 1) * LP + jn) != NO_ROOT)
+          key[2] = pair(tile_root<TR, TC, CO>(lroot, L.Ws, i + 1, jn));
         if (key[1] == key[0]) key[1] = NONE;
         if (key[2] == key[0] || key[2] == key[1]) key[2] = NONE;
       }
@@ -1014,24 +1025,24 @@ __global__ void __launch_bounds__(nt_merge<TR, NW>()) k_merge(const __grid_const
 // ---------------------------------------------------------------------------
 constexpr int NT_FLAT = 256;
 
-// Root of a chain in the (now read-only) global union-find: cached loads.
-__device__ __forceinline__ int find_ro(const int32_t* __restrict__ P, int x, int limit) {
-  int p = __ldg(P + x);
+// Root of a chain in the (now read-only) global union-find.
+template <bool CO>
+__device__ __forceinline__ int find_ro(const int32_t* P, int x, int limit) {
+  int p = ld_in<CO>(P + x);
   while (p != x && limit-- > 0) {
     x = p;
-    p = __ldg(P + x);
+    p = ld_in<CO>(P + x);
   }
   return x;
 }
 
 // Label of any vertex of the scan (used for the back-fill neighbour that lies
 // in the next tile).
-template <int TR, int TC>
-__device__ __forceinline__ int32_t vertex_label_global(const uint16_t* __restrict__ lroot,
-                                                       const int32_t* __restrict__ parent, int Ws, int W,
+template <int TR, int TC, bool CO>
+__device__ __forceinline__ int32_t vertex_label_global(const uint16_t* lroot, const int32_t* parent, int Ws, int W,
                                                        int s, int i, int j, int limit) {
-  if (lroot[(size_t)i * root_pitch(Ws) + j] == NO_ROOT) return -1;
-  const int g = find_ro(parent, tile_root<TR, TC>(lroot, Ws, i, j), limit);
+  if (ld_in<CO>(lroot + (size_t)i * root_pitch(Ws) + j) == NO_ROOT) return -1;
+  const int g = find_ro<CO>(parent, tile_root<TR, TC, CO>(lroot, Ws, i, j), limit);
   const int gi = g / Ws, gj = g - gi * Ws;
   return gi * W + gj * s;
 }
@@ -1068,7 +1079,7 @@ __device__ __forceinline__ int32_t root_label(const int32_t* lab_s, uint32_t r) 
 
 // Labels of one tile (NTB threads; fsm: FlatGeo<TR,NW>::bytes of dynamic
 // shared memory; nlist: a shared counter).
-template <int TR, int NW, int NTB>
+template <int TR, int NW, int NTB, bool CO = false>
 __device__ __forceinline__ void flatten_body(const ScanDesc* d, int lt, unsigned char* fsm, int& nlist) {
   using FG = FlatGeo<TR, NW>;
   constexpr int TC = FG::TC, NQ = FG::NQ, NWF = NTB / 32;
@@ -1079,8 +1090,8 @@ __device__ __forceinline__ void flatten_body(const ScanDesc* d, int lt, unsigned
   const int tid = threadIdx.x, lane = tid & 31, wf = tid >> 5;
   const Loc L = make_loc(d, lt, TR, TC);
   const int W = L.W, Ws = L.Ws, s = L.s;
-  const uint16_t* __restrict__ lroot = d->lroot;
-  const int32_t* __restrict__ parent = d->parent;
+  const uint16_t* lroot = d->lroot;
+  const int32_t* parent = d->parent;
   int32_t* __restrict__ labels = d->labels;
   const int limit = L.H * Ws + 1;
   if (tid == 0) nlist = 0;
@@ -1096,7 +1107,7 @@ __device__ __forceinline__ void flatten_body(const ScanDesc* d, int lt, unsigned
     uint32_t m = 0;  // which of the four are roots
     if (k < nquad) {
       uint2 r4 = make_uint2(0xFFFFFFFFu, 0xFFFFFFFFu);
-      if (q < nq) r4 = __ldg(reinterpret_cast<const uint2*>(lroot + (size_t)(L.r0 + lr) * root_pitch(Ws) + L.c0) + q);
+      if (q < nq) r4 = ld_in<CO>(reinterpret_cast<const uint2*>(lroot + (size_t)(L.r0 + lr) * root_pitch(Ws) + L.c0) + q);
       // entries past the tile's last column (the next tile's, or the row
       // padding, which nothing writes) are staged as NO_ROOT
       const int lim = L.cn - 4 * q;  // columns of the quad inside the tile
@@ -1151,7 +1162,7 @@ __device__ __forceinline__ void flatten_body(const ScanDesc* d, int lt, unsigned
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         if (k0 + q * NTB >= nl) continue;
-        const int p = __ldg(parent + x[q]);
+        const int p = ld_in<CO>(parent + x[q]);
         if (p != x[q]) {
           x[q] = p;
           more = true;
@@ -1198,7 +1209,7 @@ __device__ __forceinline__ void flatten_body(const ScanDesc* d, int lt, unsigned
   } else {
     for (int lr = wf; lr < L.rn; lr += NWF) {
       const int i = L.r0 + lr;
-      const int row = d->order[i];
+      const int row = ld_in<CO>(d->order + i);
       for (int lc = lane; lc < L.cn; lc += 32) {
         const int j = L.c0 + lc;
         const int32_t lo = root_label(lab_s, lr_s[lr * TC + lc]);
@@ -1217,7 +1228,7 @@ __device__ __forceinline__ void flatten_body(const ScanDesc* d, int lt, unsigned
           if (jh >= L.c0 && jh < L.c0 + L.cn) {
             hi = root_label(lab_s, lr_s[lr * TC + (jh - L.c0)]);
           } else {
-            hi = vertex_label_global<TR, TC>(lroot, parent, Ws, W, s, i, jh, limit);
+            hi = vertex_label_global<TR, TC, CO>(lroot, parent, Ws, W, s, i, jh, limit);
           }
         }
         const int cend = min((j + 1) * s, W);
@@ -1324,9 +1335,9 @@ __global__ void __launch_bounds__(NW * 32) k_fused(const __grid_constant__ Fused
     }
     __syncthreads();
     if (ph == PH_PREP) prep_body<NTB>(d, reinterpret_cast<float*>(smem), f.err);
-    else if (ph == PH_TILE) tile_body<TR, NW>(d, lt, smem, f.err);
-    else if (ph == PH_MERGE) merge_body<TR, NW, NTB>(d, lt, f.err);
-    else flatten_body<TR, NW, NTB>(d, lt, smem, nlist);
+    else if (ph == PH_TILE) tile_body<TR, NW, true>(d, lt, smem, f.err);
+    else if (ph == PH_MERGE) merge_body<TR, NW, NTB, true>(d, lt, f.err);
+    else flatten_body<TR, NW, NTB, true>(d, lt, smem, nlist);
     __syncthreads();
     if (threadIdx.x == 0 && ph != PH_FLAT) {
       __threadfence();  // this CTA's writes before the count that releases them

@@ -9,12 +9,15 @@
 // and output buffers but cannot let the library grow a workspace.
 //
 // How: the workspace (ring order, per-ring sin/cos, union-find parents,
-// tile-local roots and a device error word) lives in one file-scope __device__ array of fixed size,
-// created when the library is loaded on a device and held until the process
-// exits.  Host code cannot use the array's name as a device address, so the
-// first call on each device looks the address up with cudaGetSymbolAddress
-// (with that device current) and every call passes that pointer to the same
-// kernels lsg_segment uses.  No call allocates or frees anything.
+// tile-local roots and a device error word) lives in one file-scope __device__
+// array of fixed size, created when the library is loaded on a device and
+// held until the process exits.  Host code cannot use the array's name as a
+// device address, so every call looks the address up with
+// cudaGetSymbolAddress (on the current device; a host-side lookup that
+// allocates nothing) and passes that pointer to the same kernels lsg_segment
+// uses.  Looking it up on every call keeps the pointer right even after the
+// device's primary context was torn down and recreated (the module, and with
+// it the array, is then loaded anew).  No call allocates or frees anything.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -38,27 +41,28 @@ static_assert(kTrigOff % 256 == 0 && kErrOff % 256 == 0 && kParentOff % 256 == 0
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
-void* g_scratch_addr[kMaxDevices] = {};
+void* g_prepared_for[kMaxDevices] = {};  // the array's address when the kernel attributes were last set
 
 }  // namespace
 
 // The workspace itself: one copy on every device that loads the library.
 static __device__ __align__(256) unsigned char g_lsg_scratch[kScratchBytes];
 
-// Device address of g_lsg_scratch on the current device; the lookup runs once
-// per device.
+// Device address of g_lsg_scratch on the current device.  The kernels' shared
+// memory attributes are set again whenever the address differs from the one
+// seen when they were last set (a first call, or a module loaded anew).
 static lsg_status scratch_for_current_device(char** base) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LSG_E_ARG;
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_lsg_scratch);
+  if (e != cudaSuccess || p == nullptr) return LSG_E_CUDA;
   std::lock_guard<std::mutex> lock(g_setup_mu);
-  if (!g_scratch_addr[dev]) {
+  if (g_prepared_for[dev] != p) {
     if (lsg::prepare_kernels() != cudaSuccess) return LSG_E_CUDA;
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_lsg_scratch);
-    if (e != cudaSuccess || p == nullptr) return LSG_E_CUDA;
-    g_scratch_addr[dev] = p;
+    g_prepared_for[dev] = p;
   }
-  *base = static_cast<char*>(g_scratch_addr[dev]);
+  *base = static_cast<char*>(p);
   return LSG_OK;
 }
 
@@ -94,4 +98,20 @@ extern "C" lsg_status lsg_segment_noalloc(const lsg_scan* scan, const lsg_params
   if (e == cudaSuccess) e = lsg::launch_merge(LSG_TILE_16x240, a, cs, true);
   if (e == cudaSuccess) e = lsg::launch_flatten(LSG_TILE_16x240, a, cs, true);
   return e == cudaSuccess ? LSG_OK : LSG_E_CUDA;
+}
+
+// Reads and clears the device flags the last allocation-free passes on this
+// device raised, in stream order; nothing is allocated.
+extern "C" lsg_status lsg_noalloc_get_error(lsg_stream stream) {
+  char* base = nullptr;
+  lsg_status st = scratch_for_current_device(&base);
+  if (st != LSG_OK) return st;
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+  int32_t v = 0;
+  cudaError_t e = cudaMemcpyAsync(&v, base + kErrOff, sizeof(v), cudaMemcpyDeviceToHost, cs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+  if (e == cudaSuccess) e = cudaMemsetAsync(base + kErrOff, 0, sizeof(int32_t), cs);
+  if (e != cudaSuccess) return LSG_E_CUDA;
+  if (v & lsg::DERR_TIMEOUT) return LSG_E_TIMEOUT;
+  return v ? LSG_E_DEVICE : LSG_OK;
 }

@@ -107,6 +107,7 @@ def load(build: bool = True):
             "lsg_segment_stats": (ctypes.c_int, [_P, I32, I32, I32, I32, _P, _P, _P, _P, _P, _P, _P]),
             "lsg_segment_noalloc": (ctypes.c_int, [ctypes.POINTER(lsg_scan), ctypes.POINTER(lsg_params),
                                                    ctypes.POINTER(lsg_out), _P]),
+            "lsg_noalloc_get_error": (ctypes.c_int, [_P]),
             "lsg_raycast": (ctypes.c_int, [ctypes.POINTER(lsg_raycast_spec), _P, _P, _P]),
             "lsg_spin_begin": (ctypes.c_int, [_P, ctypes.POINTER(lsg_scan), ctypes.POINTER(lsg_params),
                                               ctypes.POINTER(lsg_out), ctypes.POINTER(_P), _P]),
@@ -244,6 +245,12 @@ def lsg_segment_noalloc(scan: lsg_scan, params: lsg_params, out: lsg_out, stream
     callers that may not allocate device memory.  Returns the status code."""
     return load().lsg_segment_noalloc(ctypes.byref(scan), ctypes.byref(params), ctypes.byref(out),
                                       stream or None)
+
+
+def lsg_noalloc_get_error(stream: int = 0) -> int:
+    """Waits for the stream, reads and clears the device flags of the last
+    lsg_segment_noalloc call on the current device; returns the status."""
+    return load().lsg_noalloc_get_error(stream or None)
 
 
 def lsg_spin_begin(ctx: int, scan: lsg_scan, params: lsg_params, out: lsg_out, stream: int = 0) -> int:

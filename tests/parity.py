@@ -146,3 +146,30 @@ def compare_geometry(mb_g, nrm_g, orc: O.Result, p, bounds: np.ndarray, strict=T
 def sorted_valid(scan, p, order) -> np.ndarray:
     rs = scan.range[order]
     return ((np.float32(p.r_min) < rs) & (rs <= np.float32(p.r_max))).astype(np.uint8)
+
+
+def check_outputs(ctx, scan, p, mb, nrm, lab, nseg, range_only=False, strict=True) -> Report:
+    """The CUDA path's outputs of one scan (numpy: mesh bytes, normals, labels,
+    segment count) against the oracle on the same scan: geometry within the
+    bars above; labels and segment count exact under the same mask both ways
+    (the oracle's components of the GPU mask, and ``ctx.label_from_mask`` of
+    the oracle's mask, a GPU call); everything equal when the masks agree."""
+    import torch
+    orc = O.segment_scan(scan, oracle_params(p), range_only=range_only)
+    phi_max = abs(scan.az0) + scan.cols * abs(scan.daz)
+    bounds = normal_bounds(orc, range_only, scan.range[orc.order], phi_max, p.subsample)
+    rep = compare_geometry(mb, nrm, orc, oracle_params(p), bounds, strict=strict)
+    valid = sorted_valid(scan, p, orc.order)
+    W, s, wrap = scan.cols, p.subsample, p.wrap
+    lab_o_from_g, n_o_from_g = O.label_from_mask(mb, valid, W, s, wrap)
+    assert np.array_equal(lab, lab_o_from_g)
+    assert nseg == n_o_from_g
+    dev = torch.device("cuda", 0)
+    lab_g_from_o, n_g = ctx.label_from_mask(torch.from_numpy(orc.meshbits).to(dev),
+                                            torch.from_numpy(valid).to(dev), W, s, wrap)
+    torch.cuda.synchronize()
+    assert np.array_equal(lab_g_from_o.cpu().numpy(), orc.labels)
+    assert int(n_g.cpu()[0]) == orc.nseg
+    if np.array_equal(mb, orc.meshbits):
+        assert np.array_equal(lab, orc.labels) and nseg == orc.nseg
+    return rep

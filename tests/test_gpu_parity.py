@@ -62,25 +62,7 @@ def run_gpu(ctx, scan, p, range_only=False, tile=None):
 
 def full_check(ctx, scan, p, range_only=False, tile=None, strict=True):
     mb, nrm, lab, nseg = run_gpu(ctx, scan, p, range_only, tile)
-    orc = O.segment_scan(scan, parity.oracle_params(p), range_only=range_only)
-    phi_max = abs(scan.az0) + scan.cols * abs(scan.daz)
-    bounds = parity.normal_bounds(orc, range_only, scan.range[orc.order], phi_max, p.subsample)
-    rep = parity.compare_geometry(mb, nrm, orc, parity.oracle_params(p), bounds, strict=strict)
-    valid = parity.sorted_valid(scan, p, orc.order)
-    # labels exact under the same mask, both ways
-    W, s = scan.cols, p.subsample
-    wrap = p.wrap
-    lab_o_from_g, n_o_from_g = O.label_from_mask(mb, valid, W, s, wrap)
-    assert np.array_equal(lab, lab_o_from_g)
-    assert nseg == n_o_from_g
-    dev = torch.device("cuda", 0)
-    lab_g_from_o, n_g = ctx.label_from_mask(torch.from_numpy(orc.meshbits).to(dev),
-                                            torch.from_numpy(valid).to(dev), W, s, wrap)
-    torch.cuda.synchronize()
-    assert np.array_equal(lab_g_from_o.cpu().numpy(), orc.labels)
-    assert int(n_g.cpu()[0]) == orc.nseg
-    if np.array_equal(mb, orc.meshbits):
-        assert np.array_equal(lab, orc.labels) and nseg == orc.nseg
+    rep = parity.check_outputs(ctx, scan, p, mb, nrm, lab, nseg, range_only=range_only, strict=strict)
     return rep, mb, nrm, lab, nseg
 
 

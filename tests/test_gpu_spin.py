@@ -1,6 +1,8 @@
-"""Streaming (lsg_spin_*): a revolution pushed column range by column range
-gives lsg_segment's outputs bit for bit.  Columns not yet pushed hold
-garbage, so a tile computed before its columns arrived would show."""
+"""Streaming (lsg_spin_*, Sec. 2: the mesh can be built while the sensor
+acquires the scan): a revolution pushed column range by column range gives
+lsg_segment's outputs bit for bit, and meets the oracle's parity bars on its
+own.  Columns not yet pushed hold garbage, so a tile computed before its
+columns arrived would show."""
 import math
 from dataclasses import replace
 
@@ -8,6 +10,7 @@ import numpy as np
 import pytest
 
 import lidarsim
+import parity
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -79,6 +82,45 @@ def test_spin_equals_segment(ctx, name, spec, wrap, npush, tile):
     assert torch.equal(got.nseg, want.nseg)
     spin.close()
     lsg.lsg_set_tile(ctx.h, lsg.TILES["32x240"])
+
+
+def stream_scan(ctx, scan, p, npush, seed, tile):
+    """Pushes the scan into a garbage-filled buffer in npush column ranges and
+    returns the finished outputs as numpy arrays."""
+    lsg = mod()
+    lsg.lsg_set_tile(ctx.h, lsg.TILES[tile])
+    dev = torch.device("cuda", 0)
+    elev = torch.from_numpy(scan.elev).to(dev)
+    full = torch.from_numpy(scan.xyzr).to(dev)
+    rng = np.random.default_rng(seed)
+    buf = torch.from_numpy(rng.uniform(-30, 30, size=scan.xyzr.shape).astype(np.float32)).to(dev)
+    spin = lsg.Spin(ctx, elev, xyzr=buf, az0=scan.az0, daz=scan.daz, params=p)
+    c0 = 0
+    for c1 in schedule(scan.cols, npush, rng):
+        buf[:, c0:c1] = full[:, c0:c1]
+        spin.push(c1)
+        c0 = c1
+    got = spin.finish()
+    torch.cuda.synchronize()
+    assert ctx.error() == lsg.LSG_OK
+    spin.close()
+    lsg.lsg_set_tile(ctx.h, lsg.TILES["32x240"])
+    return (got.meshbits.cpu().numpy(), got.normals.cpu().numpy(), got.labels.cpu().numpy(),
+            int(got.nseg.cpu()[0]))
+
+
+ORACLE_CASES = [c for c in CASES if c[0] in ("ring16", "w257-s3-nowrap", "w131-wrap", "w61")]
+
+
+@pytest.mark.parametrize("tile", ["32x120", "4x120"])
+@pytest.mark.parametrize("name,spec,wrap,npush", ORACLE_CASES, ids=[c[0] for c in ORACLE_CASES])
+def test_spin_meets_the_oracle(ctx, name, spec, wrap, npush, tile):
+    scan = lidarsim.make_scan(spec)
+    p = params_of(spec, wrap)
+    mb, nrm, lab, nseg = stream_scan(ctx, scan, p, npush, 7 * npush + len(name), tile)
+    rep = parity.check_outputs(ctx, scan, p, mb, nrm, lab, nseg)
+    print(f"\nstreamed {name} ({tile}): {rep}")
+    assert rep.vertices > 0
 
 
 def test_spin_argument_errors(ctx):

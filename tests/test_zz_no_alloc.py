@@ -9,7 +9,9 @@ second call finds the first call's leftovers in the shared array), and checks
 each result against lsg_segment on the same inputs with the tolerances the
 other GPU tests use: mesh bits, labels and segment count exact, normals
 within 1e-4 rad.  It also checks that a scan beyond the array's capacity is
-refused before anything is launched.
+refused before anything is launched, and that a NaN elevation (bad input the
+device sees) is reported by lsg_noalloc_get_error, which also allocates
+nothing, and cleared by reading it.
 
 The file name makes pytest collect it last; it creates its own context and
 inputs, so it also passes alone in a fresh process.
@@ -75,3 +77,24 @@ def test_noalloc_refuses_scans_beyond_its_fixed_workspace(gpu_lib):
     st = lsg.lsg_segment_noalloc(lsg.make_scan(elev, xyzr, None, 0.0, 2 * math.pi / W), lsg.Params().to_c(),
                                  out.to_c(), torch.cuda.current_stream().cuda_stream)
     assert st == lsg.LSG_E_SHAPE
+
+
+def test_noalloc_reports_device_flags_through_its_error_query(gpu_lib):
+    from paper_2005_02704_gb300 import lsg
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream().cuda_stream
+    spec = lidarsim.ring16(cols=128)
+    scan = lidarsim.make_scan(spec)
+    p = _params(spec)
+    xyzr = torch.from_numpy(scan.xyzr).to(dev)
+    out = lsg.alloc_outputs(scan.rings, scan.cols, p.subsample, dev)
+    good = torch.from_numpy(scan.elev).to(dev)
+    bad = good.clone()
+    bad[3] = float("nan")
+    st = lsg.lsg_segment_noalloc(lsg.make_scan(bad, xyzr, None, scan.az0, scan.daz), p.to_c(), out.to_c(), stream)
+    assert st == lsg.LSG_OK
+    assert lsg.lsg_noalloc_get_error(stream) == lsg.LSG_E_DEVICE
+    assert lsg.lsg_noalloc_get_error(stream) == lsg.LSG_OK  # cleared by reading it
+    st = lsg.lsg_segment_noalloc(lsg.make_scan(good, xyzr, None, scan.az0, scan.daz), p.to_c(), out.to_c(), stream)
+    assert st == lsg.LSG_OK
+    assert lsg.lsg_noalloc_get_error(stream) == lsg.LSG_OK
