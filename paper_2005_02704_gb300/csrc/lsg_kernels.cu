@@ -363,20 +363,22 @@ __device__ __forceinline__ void jump_cut2(float2 rp, float2 rq, float2 tau, bool
   cb = fabsf(dd.y) > t.y;
 }
 
-// One weighted triangle term of two vertices' normal sums (Sec. 2, normal
-// estimation): w (a x b) with w = 1 / (|a| + |b|), times the triangle's
-// existence (exactly 0 or 1).  Points out of range have zero coordinates, so
-// every spoke is finite and a missing triangle's term is an exact zero.
-__device__ __forceinline__ void tri2(float2 ax, float2 ay, float2 az, float2 la, float2 bx, float2 by, float2 bz,
-                                     float2 lb, float2 ex, float2& sx, float2& sy, float2& sz) {
+// Cross product a x b of two pairs of vectors.
+__device__ __forceinline__ void cross2(float2 ax, float2 ay, float2 az, float2 bx, float2 by, float2 bz, float2& cx,
+                                       float2& cy, float2& cz) {
+  cx = fma2(ay, bz, mul2(neg2(az), by));
+  cy = fma2(az, bx, mul2(neg2(ax), bz));
+  cz = fma2(ax, by, mul2(neg2(ay), bx));
+}
+
+// Weight of a triangle at one of its vertices (Sec. 2, normal estimation):
+// 1 / (|a| + |b|) for the vertex's two spokes a, b along the triangle's
+// edges, times the triangle's existence (exactly 0 or 1).  Points out of
+// range have zero coordinates, so every spoke is finite and a missing
+// triangle's term is an exact zero.
+__device__ __forceinline__ float2 weight2(float2 la, float2 lb, float2 ex) {
   const float2 l = add2(la, lb);
-  const float2 wt = mul2(make_float2(rcp_approx(l.x), rcp_approx(l.y)), ex);
-  const float2 cx = fma2(ay, bz, mul2(neg2(az), by));
-  const float2 cy = fma2(az, bx, mul2(neg2(ax), bz));
-  const float2 cz = fma2(ax, by, mul2(neg2(ay), bx));
-  sx = fma2(wt, cx, sx);
-  sy = fma2(wt, cy, sy);
-  sz = fma2(wt, cz, sz);
+  return mul2(make_float2(rcp_approx(l.x), rcp_approx(l.y)), ex);
 }
 
 // Homogeneity predicate of Algorithm 1 for two vertex pairs.  A vertex
@@ -526,21 +528,35 @@ __device__ __forceinline__ void tile_sweep(const ScanDesc* __restrict__ d, const
            ((((RA ? B_R : 0u) | (vA ? B_VALID : 0u)) | (((RB ? B_R : 0u) | (vB ? B_VALID : 0u)) << 8)) << 16);
     // triangle existence as exact 0 / 1 products: the lower (d, g, r) and
     // upper (g, r above, d to the right) triangles of each column's quad
-    // between rows k-1 and k, and the same two of the quad to its left
+    // between rows k-1 and k
     const float2 eD = make_float2(DA ? 1.f : 0.f, DB ? 1.f : 0.f);
     const float2 eG = make_float2(GA ? 1.f : 0.f, GB ? 1.f : 0.f);
     const float2 eR = make_float2(RA ? 1.f : 0.f, RB ? 1.f : 0.f);
     const float2 tLo = mul2(mul2(eD, eG), eR);
     const float2 tUp = mul2(mul2(eG, er1), right_of(eD));
-    const float2 tLoL = left_of(tLo), tUpL = left_of(tUp);
-    // R edges of row k-1 ending at each column (below: F of row k-1)
-    const float2 fx1 = left_of(rx1), fy1 = left_of(ry1), fz1 = left_of(rz1), lf1 = left_of(lr1);
+    // Each triangle's cross product once, shared by its three vertices (the
+    // spokes' cross products of the paper's six terms are the same vector
+    // for every corner of a triangle): lower (p, q, q') = (k-1 c, k c,
+    // k c+1): d x r; upper (p, q', p') = (k-1 c, k c+1, k-1 c+1): d' x r1,
+    // with d' the D edge of the column to the right.  The two edges at the
+    // right angle are the shortest, so the product's rounding error is no
+    // larger than that of any corner's own two spokes.
+    const float2 drx = right_of(dx), dry = right_of(dy), drz = right_of(dz), ldr = right_of(ld);
+    float2 lox, loy, loz, upx, upy, upz;
+    cross2(dx, dy, dz, ex, ey, ez, lox, loy, loz);
+    cross2(drx, dry, drz, rx1, ry1, rz1, upx, upy, upz);
+    // the weights at each corner: 1 / (sum of the corner's two spokes)
+    const float2 wLp = weight2(ld, lg, tLo), wLq = weight2(ld, le, tLo), wLr = weight2(lg, le, tLo);
+    const float2 wUp = weight2(lg, lr1, tUp), wUr = weight2(lr1, ldr, tUp), wUq = weight2(ldr, lg, tUp);
 
-    // normals of row k-1: the three terms below it
-    float2 sx = ux, sy = uy, sz = uz;
-    tri2(dx, dy, dz, ld, gx, gy, gz, lg, tLo, sx, sy, sz);
-    tri2(gx, gy, gz, lg, rx1, ry1, rz1, lr1, tUp, sx, sy, sz);
-    tri2(dx, dy, dz, ld, fx1, fy1, fz1, lf1, tUpL, sx, sy, sz);
+    // normals of row k-1: its own quads' lower and upper triangles, and the
+    // upper triangle of the quad to its left (corner p', one lane over)
+    float2 sx = fma2(wLp, lox, fma2(wUp, upx, ux));
+    float2 sy = fma2(wLp, loy, fma2(wUp, upy, uy));
+    float2 sz = fma2(wLp, loz, fma2(wUp, upz, uz));
+    sx = add2(sx, left_of(mul2(wUr, upx)));
+    sy = add2(sy, left_of(mul2(wUr, upy)));
+    sz = add2(sz, left_of(mul2(wUr, upz)));
     const float2 q2 = fma2(sx, sx, fma2(sy, sy, mul2(sz, sz)));
     // a sum shorter than 2^-63 counts as no normal (as does a zero sum, which
     // is what a vertex out of range has: none of its triangles exists)
@@ -550,17 +566,12 @@ __device__ __forceinline__ void tile_sweep(const ScanDesc* __restrict__ d, const
     const float2 nx1 = mul2(sx, fn), ny1 = mul2(sy, fn), nz1 = mul2(sz, fn);
     const uint32_t m1 = (win & 0xffffu) | (hA ? (uint32_t)B_HASN : 0u) | (hB ? (uint32_t)B_HASN << 8 : 0u);
 
-    // normals of row k: the three terms above it
-    {
-      const float2 fx = left_of(ex), fy = left_of(ey), fz = left_of(ez), lf = left_of(le);
-      const float2 glx = left_of(gx), gly = left_of(gy), glz = left_of(gz), lgl = left_of(lg);
-      ux = Z2;
-      uy = Z2;
-      uz = Z2;
-      tri2(dx, dy, dz, ld, ex, ey, ez, le, tLo, ux, uy, uz);
-      tri2(dx, dy, dz, ld, glx, gly, glz, lgl, tUpL, ux, uy, uz);
-      tri2(glx, gly, glz, lgl, fx, fy, fz, lf, tLoL, ux, uy, uz);
-    }
+    // normals of row k, the terms through row k-1: its own quads' lower
+    // triangles (corner q), and the lower and upper triangles of the quad to
+    // its left (corner q', one lane over)
+    ux = fma2(wLq, lox, left_of(fma2(wLr, lox, mul2(wUq, upx))));
+    uy = fma2(wLq, loy, left_of(fma2(wLr, loy, mul2(wUq, upy))));
+    uz = fma2(wLq, loz, left_of(fma2(wLr, loz, mul2(wUq, upz))));
 
     // homogeneity mask and outputs of row k-2
     if (hr >= 3) {
