@@ -9,10 +9,11 @@ kernels) with inputs resident in HBM.  Inputs are larger than L2, so no flush
 is needed between steps.
 
 The JSON line reports points/s of the batched path (value), the same metric
-end to end through the C ABI with host buffers (e2e: host->device copy of the
-inputs, the pass, device->host copy of labels and segment counts, in chunks
-whose copies overlap the other chunks' passes; the one-after-the-other
-variant is reported beside it), the plain
+end to end through the C ABI with host buffers (e2e: lsg_batch_plan_io, one
+graph replay per step that copies the inputs from pinned host memory, runs
+the pass and copies every output back, in chunks whose copies overlap the
+other chunks' passes; the one-chunk variant and the host link's floor for the
+same bytes are reported beside it), the plain
 per-scan path (one lsg_segment call per scan), the dominant kernel's HBM
 roofline fraction, and the FP64 oracle timed on the host cores on a bounded
 sample (cpu_baseline).
@@ -595,49 +596,73 @@ def main():
         plan.set_schedule(2)
 
     # ---- end to end through the C ABI with host buffers --------------------
-    # (a) the pipelined host path: chunks of scans whose copies in both
-    #     directions overlap the other chunks' passes; (b) for reference, the
-    #     same copies and the single-plan pass queued one after the other
-    #     The host loop runs with the cyclic collector paused; the median of
-    #     three timed regions of K steps each is reported (host-side jitter
-    #     stretches single regions)
+    # lsg_batch_plan_io: one graph replay per step copies every scan's inputs
+    # from pinned host memory, runs the pass and copies every output (labels,
+    # segment counts, mesh bytes, normals) back, in chunks whose copies in
+    # both directions overlap the other chunks' passes; K replays between
+    # events on the launching stream, median of three timed regions.  Also:
+    # the same with one chunk (copies, pass and copies one after the other),
+    # and the host link's floor for the same bytes (the input copy and the
+    # output copy on two streams at once, nothing else).
     from paper_2005_02704_gb300 import serve
-    pipe = db.pipeline(ctx, plan.tile, chunks=args.e2e_chunks, schedule=schedule)
-    for _ in range(max(args.warmup, 3)):
-        pipe.step(stream)
-    h2d = d2h = 0
-    regions = []
-    with serve.no_gc_pauses():
-        for _ in range(3):
-            torch.cuda.synchronize()
-            barrier()
+
+    def time_e2e(p_io):
+        for _ in range(max(args.warmup, 3)):
+            p_io.run(stream)
+        regions = []
+        with serve.no_gc_pauses():
+            for _ in range(3):
+                torch.cuda.synchronize()
+                barrier()
+                torch.cuda.synchronize()
+                e0.record(stream)
+                for _ in range(args.steps):
+                    p_io.run(stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                barrier()
+                regions.append(max_over_ranks(e0.elapsed_time(e1) / args.steps))
+        if ctx.error() != lsg.LSG_OK:
+            raise RuntimeError("device error in the end-to-end measurement")
+        return statistics.median(regions), regions
+
+    def link_floor(dbx):
+        s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+        outs_h = (dbx.h_lab, dbx.h_nseg, dbx.h_mb, dbx.h_nrm)
+        outs_d = (dbx.d_lab, dbx.d_nseg, dbx.d_mb, dbx.d_nrm)
+        ts = []
+        for k in range(4):
             torch.cuda.synchronize()
             e0.record(stream)
-            for _ in range(args.steps):
-                h2d, d2h = pipe.step(stream)
+            s_in.wait_stream(stream)
+            s_out.wait_stream(stream)
+            with torch.cuda.stream(s_in):
+                dbx.d_in.copy_(dbx.h_in, non_blocking=True)
+                dbx.d_elev.copy_(dbx.h_elev, non_blocking=True)
+            with torch.cuda.stream(s_out):
+                for h, d_ in zip(outs_h, outs_d):
+                    h.copy_(d_, non_blocking=True)
+            stream.wait_stream(s_in)
+            stream.wait_stream(s_out)
             e1.record(stream)
             torch.cuda.synchronize()
-            barrier()
-            regions.append(max_over_ranks(e0.elapsed_time(e1) / args.steps))
-    ms_e2e = statistics.median(regions)
+            if k:
+                ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    plan_io = db.plan_io(ctx, plan.tile, chunks=args.e2e_chunks)
+    h2d, d2h = plan_io.io_bytes()
+    ms_e2e, regions = time_e2e(plan_io)
     e2e_value = pts_all / (ms_e2e / 1e3)
-    pipe.close()
-    for _ in range(max(args.warmup, 3)):
-        db.upload()
-        plan.run()
-        db.download()
+    e2e_launches = plan_io.launches
+    plan_io.close()
+    plan_io1 = db.plan_io(ctx, plan.tile, chunks=1)
+    ms_e2e_serial, _ = time_e2e(plan_io1)
+    plan_io1.close()
+    ms_floor = max_over_ranks(link_floor(db))
+    # the device plan's outputs again (the host-buffer replays rewrote them)
+    plan.run()
     torch.cuda.synchronize()
-    barrier()
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(args.steps):
-        db.upload()
-        plan.run()
-        db.download()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    ms_e2e_serial = max_over_ranks(e0.elapsed_time(e1) / args.steps)
 
     # ---- the same batch as ranges only (the sensor's own output form) -------
     #     x,y,z decoded on the GPU from the ring elevation and column azimuth:
@@ -662,27 +687,10 @@ def main():
         torch.cuda.synchronize()
         barrier()
         ms_r = max_over_ranks(e0.elapsed_time(e1) / args.steps)
-        piper = dbr.pipeline(ctx, plan.tile, chunks=args.e2e_chunks, schedule=schedule)
-        for _ in range(max(args.warmup, 3)):
-            piper.step(stream)
-        regions_r = []
-        h2d_r = d2h_r = 0
-        with serve.no_gc_pauses():
-            for _ in range(3):
-                torch.cuda.synchronize()
-                barrier()
-                torch.cuda.synchronize()
-                e0.record(stream)
-                for _ in range(args.steps):
-                    h2d_r, d2h_r = piper.step(stream)
-                e1.record(stream)
-                torch.cuda.synchronize()
-                barrier()
-                regions_r.append(max_over_ranks(e0.elapsed_time(e1) / args.steps))
-        if ctx.error() != lsg.LSG_OK:
-            raise RuntimeError("device error in the range-input measurement")
-        ms_er = statistics.median(regions_r)
-        piper.close()
+        pior = dbr.plan_io(ctx, plan.tile, chunks=args.e2e_chunks)
+        h2d_r, d2h_r = pior.io_bytes()
+        ms_er, regions_r = time_e2e(pior)
+        pior.close()
         planr.close()
         del dbr
         range_input = {"workload": "the same 512 scans, range float32 per point (x,y,z decoded on the GPU)",
@@ -691,7 +699,9 @@ def main():
                        "e2e": {"value": pts_all / (ms_er / 1e3), "unit": UNIT, "ms_per_step": ms_er,
                                "ms_per_step_regions": regions_r, "h2d_bytes_per_step": h2d_r,
                                "d2h_bytes_per_step": d2h_r,
-                               "path": f"HostPipeline, {args.e2e_chunks} chunks, 3 streams"}}
+                               "path": f"lsg_batch_plan_io + lsg_batch_run (C ABI), {args.e2e_chunks} chunks; "
+                                       "ranges and elevations in, labels, segment counts, mesh bytes and "
+                                       "normals out"}}
 
     # ---- plain per-scan path: one lsg_segment call per scan ----------------
     plain = None
@@ -810,10 +820,17 @@ def main():
                           {"ring_order": phase[0], "tile": phase[1], "merge": phase[2], "labels": phase[3]}),
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "ms_per_step": ms_e2e, "path": f"HostPipeline, {args.e2e_chunks} chunks, 3 streams",
-                    "ms_per_step_regions": regions,
+                    "ms_per_step": ms_e2e,
+                    "path": f"lsg_batch_plan_io + lsg_batch_run (C ABI) from pinned host buffers, "
+                            f"{args.e2e_chunks} chunks in one graph: x,y,z,r and elevations in; labels, segment "
+                            "counts, mesh bytes and normals out",
+                    "ms_per_step_regions": regions, "gpu_launches_per_step": e2e_launches,
                     "serial_ms_per_step": ms_e2e_serial,
-                    "serial_value": pts_all / (ms_e2e_serial / 1e3)},
+                    "serial_value": pts_all / (ms_e2e_serial / 1e3),
+                    "serial_path": "the same plan with one chunk (copy in, pass, copy out in sequence)",
+                    "link_floor_ms": ms_floor,
+                    "link_floor_note": "the same bytes copied host->device and device->host on two streams at "
+                                       "once, nothing else (torch copies of the pinned mirrors)"},
             "batched_latency": batched_latency,
             "range_input": range_input,
             "plain": plain,

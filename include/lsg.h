@@ -235,21 +235,29 @@ lsg_status lsg_label_from_mask(lsg_ctx* ctx, int32_t H, int32_t W, int32_t s, in
 lsg_status lsg_batch_plan(lsg_ctx* ctx, int32_t n, const lsg_scan* scans, const lsg_params* params,
                           const lsg_out* outs, int tile, lsg_plan** plan);
 
+/* Device bytes the context holds now (workspace, descriptor staging, error
+ * word, and the plans and spins made from it); 0 for NULL. */
+size_t lsg_memory_used(const lsg_ctx* ctx);
+
 /*
  * Dynamic batch: one pass over n scans whose set changes from call to call
  * (the serving path).  Same semantics and outputs as n lsg_segment calls, in
  * four launches; the scans' descriptors go to the device through a pinned
  * staging buffer of the context (two of them, alternated; a call waits until
  * the copy out of the buffer it reuses has run).  The workspace of all n scans
- * comes from the context, so one context serves one stream at a time.
+ * comes from the context, so one context serves one stream at a time.  A
+ * batch of one runs as lsg_segment does (descriptor by value, no staging).
  */
 lsg_status lsg_batch_launch(lsg_ctx* ctx, int32_t n, const lsg_scan* scans, const lsg_params* params,
                             const lsg_out* outs, lsg_stream stream);
 
-/* Host buffers of one scan for lsg_batch_launch_io (pinned memory lets the
- * copies run asynchronously; any NULL output is skipped). */
+/* Host buffers of one scan for lsg_batch_launch_io and lsg_batch_plan_io
+ * (pinned memory lets the copies run asynchronously; any NULL output is
+ * skipped). */
 typedef struct {
-  const float* xyzr;      /* host [H][W][4] input */
+  const float* xyzr;      /* host input in the scan's form: [H][W][4] x,y,z,r
+                             (lsg_scan.xyzr set), or [H][W] ranges (lsg_scan.range
+                             set) */
   const float* elevation; /* host [H] input */
   int32_t* labels;        /* host [H][W] result, or NULL */
   int32_t* nseg;          /* host [1] result, or NULL */
@@ -259,10 +267,11 @@ typedef struct {
 
 /*
  * lsg_batch_launch with the host transfers of the serving path in the same
- * call, all ordered on `stream`: every scan's x,y,z,r and elevations are
- * copied from io[b] into the device buffers scans[b].xyzr and
- * scans[b].elevation (which must be writable device memory), then the pass
- * runs, then the results listed in io[b] are copied back.
+ * call, all ordered on `stream`: every scan's input (x,y,z,r, or ranges for
+ * a range-only scan) and elevations are copied from io[b] into the device
+ * buffers scans[b].xyzr (or .range) and scans[b].elevation (which must be
+ * writable device memory), then the pass runs, then the results listed in
+ * io[b] are copied back.
  */
 lsg_status lsg_batch_launch_io(lsg_ctx* ctx, int32_t n, const lsg_scan* scans, const lsg_params* params,
                                const lsg_out* outs, const lsg_host_io* io, lsg_stream stream);
@@ -318,6 +327,38 @@ lsg_status lsg_plan_phase_times(lsg_plan* plan, float* ms);
 
 /* Frees the plan (synchronises the device first). */
 lsg_status lsg_plan_destroy(lsg_plan* plan);
+
+/*
+ * Batched path from and to host memory (the problem of Sec. 2 end to end: a
+ * scan with its ring elevations goes in, the mesh, normals and labels come
+ * out).  Like lsg_batch_plan, plus the host transfers in the captured graph:
+ * the batch is cut into `chunks` runs of consecutive scans with about equal
+ * point counts; for each, the inputs io[b].xyzr and io[b].elevation are
+ * copied into the device buffers scans[b] (x,y,z,r or ranges, by the scan's
+ * form, and the elevations, all of which must be writable device memory),
+ * the chunk's pass runs once they have landed, and the chunk's outputs are
+ * copied into io[b].labels, .nseg, .meshbits and .normals (NULL ones
+ * skipped) once its pass is done; the copies of neighbouring chunks, in both
+ * directions, run under each chunk's pass.  Consecutive scans whose host and
+ * device buffers are contiguous share one copy.  lsg_batch_run replays the
+ * whole sequence; the host outputs are complete once the stream has
+ * synchronised, and the host inputs may be rewritten after that.
+ *   io[n]      host buffers of every scan: page-locked memory (cudaHostAlloc
+ *              or cudaHostRegister), else LSG_E_ARG; not copied, must
+ *              outlive the plan.
+ *   chunks     >= 1 (at most n are used).
+ *   tile       as for lsg_batch_plan.
+ * The plan runs the phased kernels per chunk; lsg_plan_set_fused accepts
+ * only 0 for it, lsg_autotune tries the tile shapes, and
+ * lsg_plan_phase_times gives the whole run in ms[0].
+ */
+lsg_status lsg_batch_plan_io(lsg_ctx* ctx, int32_t n, const lsg_scan* scans, const lsg_params* params,
+                             const lsg_out* outs, const lsg_host_io* io, int32_t chunks, int tile,
+                             lsg_plan** plan);
+
+/* Bytes one run of a host-buffer plan copies host -> device (*h2d) and
+ * device -> host (*d2h); LSG_E_ARG for a device-resident plan. */
+lsg_status lsg_plan_io_bytes(const lsg_plan* plan, size_t* h2d, size_t* d2h);
 
 /* Reads and clears the context's sticky device error word (synchronises the
  * device).  LSG_OK when no device-side error was recorded. */

@@ -5,10 +5,11 @@ All scans' inputs live in one device buffer (x,y,z,r float32, 16-byte
 aligned per scan, or, for range-only decoding, the ranges alone) plus one
 buffer of elevations; all outputs in one buffer per kind.  ``lsg_scan`` / ``lsg_out`` descriptors point into them, so one
 ``lsg_batch_plan`` covers the whole batch and replays stay valid as long as
-the buffers live.  A pinned host mirror of the inputs and of the labels and
-segment counts serves the end-to-end (host -> device -> host) path, which
-``HostPipeline`` runs in chunks so that copies in both directions overlap the
-passes.
+the buffers live.  A pinned host mirror of the inputs and of every output
+(labels, segment counts, mesh bytes, normals) serves the end-to-end path,
+``lsg_batch_plan_io``: one captured graph per step that copies the inputs in,
+runs the pass and copies every output back, in chunks whose copies in both
+directions overlap the other chunks' passes.
 """
 from __future__ import annotations
 
@@ -76,6 +77,8 @@ class DeviceBatch:
         self.h_elev = torch.empty(max(E, 1), dtype=f32, pin_memory=pinned)
         self.h_lab = torch.empty(max(P, 1), dtype=i32, pin_memory=pinned)
         self.h_nseg = torch.empty(max(self.n, 1), dtype=i32, pin_memory=pinned)
+        self.h_mb = torch.empty(max(V, 1), dtype=u8, pin_memory=pinned)
+        self.h_nrm = torch.empty((max(V, 1), 3), dtype=f32, pin_memory=pinned)
         self.az0 = np.zeros(self.n, np.float32)
         self.daz = np.zeros(self.n, np.float32)
 
@@ -142,9 +145,27 @@ class DeviceBatch:
     def plan(self, ctx: "lsg.Context", tile: int = lsg.LSG_TILE_AUTO) -> "lsg.BatchPlan":
         return lsg.BatchPlan(ctx, self.c_scans(), self.c_params(), self.c_outs(), tile)
 
-    def pipeline(self, ctx: "lsg.Context", tile: int = lsg.LSG_TILE_AUTO, chunks: int = 8,
-                 schedule=None) -> "HostPipeline":
-        return HostPipeline(self, ctx, tile, chunks, schedule)
+    def c_host_io(self) -> List["lsg.lsg_host_io"]:
+        """Host buffers of every scan in the pinned mirrors (inputs in the
+        batch's form, every output)."""
+        out = []
+        for b, sh in enumerate(self.shapes):
+            io = lsg.lsg_host_io()
+            p0, v0, e0 = int(self.pt_off[b]), int(self.v_off[b]), int(self.e_off[b])
+            io.xyzr = self.h_in.data_ptr() + 4 * self.in_width * p0 if sh.points else None
+            io.elevation = self.h_elev.data_ptr() + 4 * e0 if sh.rings else None
+            io.labels = self.h_lab.data_ptr() + 4 * p0 if sh.points else None
+            io.nseg = self.h_nseg.data_ptr() + 4 * b
+            io.meshbits = self.h_mb.data_ptr() + v0 if sh.vertices else None
+            io.normals = self.h_nrm.data_ptr() + 12 * v0 if sh.vertices else None
+            out.append(io)
+        return out
+
+    def plan_io(self, ctx: "lsg.Context", tile: int = lsg.LSG_TILE_AUTO, chunks: int = 16) -> "lsg.BatchPlan":
+        """The end-to-end plan: host inputs in, every output back to the
+        pinned host mirrors, in one graph replay per step."""
+        return lsg.BatchPlan(ctx, self.c_scans(), self.c_params(), self.c_outs(), tile, io=self.c_host_io(),
+                             chunks=chunks)
 
     # ---- per-scan views of the device outputs -----------------------------
     def view(self, b: int):
@@ -161,78 +182,6 @@ class DeviceBatch:
         if self.form == "range":
             return self.d_elev[e0:e1], self.d_in[p0:p1].view(sh.rings, sh.cols)
         return self.d_elev[e0:e1], self.d_in[p0:p1].view(sh.rings, sh.cols, 4)
-
-
-class HostPipeline:
-    """End-to-end passes from the pinned host mirror, in chunks that overlap.
-
-    The batch is cut into ``chunks`` runs of consecutive scans with about
-    equal point counts, each with its own captured plan.  In a step, chunk c's
-    inputs go host -> device on one stream, its pass runs on a second stream
-    once they have landed, and its labels and segment counts go device ->
-    host on a third once the pass is done, so the copies of the neighbouring
-    chunks, in both directions, run under each chunk's pass.  A step starts
-    after the work already queued on the caller's stream and the caller's
-    stream waits for its last copy.
-    """
-
-    def __init__(self, db: DeviceBatch, ctx: "lsg.Context", tile: int = lsg.LSG_TILE_AUTO, chunks: int = 8,
-                 schedule=None):
-        torch = db.torch
-        self.db = db
-        n = db.n
-        chunks = max(1, min(int(chunks), n))
-        bounds = [0]
-        for c in range(1, chunks):
-            b = int(np.searchsorted(db.pt_off, db.points * c / chunks))
-            b = max(bounds[-1] + 1, min(b, n - (chunks - c)))
-            bounds.append(b)
-        bounds.append(n)
-        self.ranges = [(b0, b1) for b0, b1 in zip(bounds[:-1], bounds[1:]) if b1 > b0]
-        scans, params, outs = db.c_scans(), db.c_params(), db.c_outs()
-        self.plans = [lsg.BatchPlan(ctx, scans[b0:b1], params[b0:b1], outs[b0:b1], tile) for b0, b1 in self.ranges]
-        if schedule is not None:
-            for p in self.plans:
-                p.set_schedule(int(schedule))
-        self.s_in = torch.cuda.Stream(db.dev)
-        self.s_run = torch.cuda.Stream(db.dev)
-        self.s_out = torch.cuda.Stream(db.dev)
-        self.ev_in = [torch.cuda.Event() for _ in self.ranges]
-        self.ev_run = [torch.cuda.Event() for _ in self.ranges]
-        self.ev_out = torch.cuda.Event()
-
-    def step(self, stream=None):
-        """One end-to-end pass; returns (host->device bytes, device->host bytes)."""
-        torch, db = self.db.torch, self.db
-        cur = stream if stream is not None else torch.cuda.current_stream(db.dev)
-        self.s_in.wait_stream(cur)
-        self.s_run.wait_stream(cur)
-        self.s_out.wait_stream(cur)
-        with torch.cuda.stream(self.s_in):
-            db.d_elev.copy_(db.h_elev, non_blocking=True)
-        h2d, d2h = db.h_elev.numel() * 4, 0
-        for c, (b0, b1) in enumerate(self.ranges):
-            p0, p1 = int(db.pt_off[b0]), int(db.pt_off[b1])
-            with torch.cuda.stream(self.s_in):
-                db.d_in[p0:p1].copy_(db.h_in[p0:p1], non_blocking=True)
-                self.ev_in[c].record(self.s_in)
-            self.s_run.wait_event(self.ev_in[c])
-            self.plans[c].run(stream=self.s_run)
-            self.ev_run[c].record(self.s_run)
-            self.s_out.wait_event(self.ev_run[c])
-            with torch.cuda.stream(self.s_out):
-                db.h_lab[p0:p1].copy_(db.d_lab[p0:p1], non_blocking=True)
-                db.h_nseg[b0:b1].copy_(db.d_nseg[b0:b1], non_blocking=True)
-            h2d += (p1 - p0) * 4 * db.in_width
-            d2h += (p1 - p0) * 4 + (b1 - b0) * 4
-        self.ev_out.record(self.s_out)
-        cur.wait_event(self.ev_out)
-        return h2d, d2h
-
-    def close(self) -> None:
-        for p in self.plans:
-            p.close()
-        self.plans = []
 
 
 class _null:

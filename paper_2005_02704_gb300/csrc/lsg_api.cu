@@ -55,6 +55,13 @@ struct lsg_plan {
   int32_t nitems = 0;
   int32_t* d_counters = nullptr;    // [1 + 3n] fused progress counters
   int launches = 0;                 // kernel launches in one replay of the graph
+  // host-buffer plans (lsg_batch_plan_io): the scans' device buffers and host
+  // buffers, and the number of chunks the copies and passes are cut into
+  int chunks = 0;                   // 0: device-resident plan
+  std::vector<lsg_scan> dev_in;     // device inputs of each scan
+  std::vector<lsg_out> dev_out;     // device outputs of each scan
+  std::vector<lsg_host_io> io;      // host buffers of each scan
+  size_t h2d_bytes = 0, d2h_bytes = 0;  // host transfers of one run
 };
 
 namespace {
@@ -286,6 +293,8 @@ lsg_status lsg_destroy(lsg_ctx* ctx) {
   return LSG_OK;
 }
 
+size_t lsg_memory_used(const lsg_ctx* ctx) { return ctx ? ctx->used : 0; }
+
 lsg_status lsg_set_tile(lsg_ctx* ctx, int tile) {
   if (!ctx) return LSG_E_ARG;
   if (tile != LSG_TILE_AUTO && (tile < 0 || tile >= LSG_TILE_COUNT)) return LSG_E_ARG;
@@ -434,6 +443,62 @@ lsg_status lsg_batch_launch_io(lsg_ctx* ctx, int32_t n, const lsg_scan* scans, c
   return batch_launch(ctx, n, scans, params, outs, io, stream);
 }
 
+// Host -> device copies of one scan's inputs (x,y,z,r or ranges, and the
+// elevations) from its host buffers.
+static cudaError_t copy_in(const lsg_scan& sc, const lsg_host_io& io, cudaStream_t cs) {
+  const size_t pts = (size_t)sc.rings * sc.cols;
+  if (!pts) return cudaSuccess;
+  cudaError_t e = sc.xyzr ? cudaMemcpyAsync(const_cast<float*>(sc.xyzr), io.xyzr, pts * 16, cudaMemcpyHostToDevice, cs)
+                          : cudaMemcpyAsync(const_cast<float*>(sc.range), io.xyzr, pts * 4, cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(const_cast<float*>(sc.elevation), io.elevation, sizeof(float) * sc.rings,
+                        cudaMemcpyHostToDevice, cs);
+  return e;
+}
+
+// Device -> host copies of the results io lists.
+static cudaError_t copy_out(const lsg_scan& sc, int Ws, const lsg_out& o, const lsg_host_io& io, cudaStream_t cs) {
+  const size_t pts = (size_t)sc.rings * sc.cols, nv = (size_t)sc.rings * Ws;
+  cudaError_t e = cudaSuccess;
+  if (io.nseg) e = cudaMemcpyAsync(io.nseg, o.nseg, sizeof(int32_t), cudaMemcpyDeviceToHost, cs);
+  if (e == cudaSuccess && io.labels && pts) e = cudaMemcpyAsync(io.labels, o.labels, pts * 4, cudaMemcpyDeviceToHost, cs);
+  if (e == cudaSuccess && io.meshbits && nv) e = cudaMemcpyAsync(io.meshbits, o.meshbits, nv, cudaMemcpyDeviceToHost, cs);
+  if (e == cudaSuccess && io.normals && nv)
+    e = cudaMemcpyAsync(io.normals, o.normals, nv * 12, cudaMemcpyDeviceToHost, cs);
+  return e;
+}
+
+// A batch of one: the single-scan pass (descriptor passed by value, kernels
+// as programmatic dependents), with the host copies when io is given.
+static lsg_status launch_one(lsg_ctx* ctx, const lsg_scan* sc, const lsg_params* p, const lsg_out* o,
+                             const lsg_host_io* io, int Ws, int tile, lsg_stream stream) {
+  DeviceGuard g(ctx->device);
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+  if (io) {
+    if (sc->rings > 0 && sc->cols > 0 && (!io->xyzr || !io->elevation)) return LSG_E_ARG;
+    const cudaError_t e = copy_in(*sc, *io, cs);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  lsg_status st = LSG_OK;
+  if (sc->rings == 0 || sc->cols == 0) {
+    st = cuda_status(cudaMemsetAsync(o->nseg, 0, sizeof(int32_t), cs));
+  } else {
+    st = reserve(ctx, scan_ws_bytes(sc->rings, Ws));
+    if (st != LSG_OK) return st;
+    KArgs a;
+    memset(&a, 0, sizeof(a));
+    a.one = make_desc(sc, p, o, Ws);
+    set_tiles(a.one, tile, 0);
+    carve_ws(a.one, static_cast<char*>(ctx->ws));
+    a.ntiles = a.one.tiles_r * a.one.tiles_c;
+    a.nscans = 1;
+    a.err = ctx->d_err;
+    st = run_pass(a, tile, true, cs);
+  }
+  if (st == LSG_OK && io) st = cuda_status(copy_out(*sc, Ws, *o, *io, cs));
+  return st;
+}
+
 static lsg_status batch_launch(lsg_ctx* ctx, int32_t n, const lsg_scan* scans, const lsg_params* params,
                                const lsg_out* outs, const lsg_host_io* io, lsg_stream stream) {
   if (!ctx || n < 1 || !scans || !params || !outs) return LSG_E_ARG;
@@ -447,6 +512,7 @@ static lsg_status batch_launch(lsg_ctx* ctx, int32_t n, const lsg_scan* scans, c
     Hs[b] = scans[b].cols > 0 ? scans[b].rings : 0;
   }
   const int tile = ctx_tile(ctx, Hs.data(), Ws.data(), n);
+  if (n == 1) return launch_one(ctx, scans, params, outs, io, Ws[0], tile, stream);
   const TileShape ts = tile_shape(tile);
   for (int b = 0; b < n; ++b)
     if (Hs[b] > 0 && Ws[b] > 0)
@@ -470,15 +536,9 @@ static lsg_status batch_launch(lsg_ctx* ctx, int32_t n, const lsg_scan* scans, c
     return cuda_status(e);
   if (io) {
     // inputs host -> device, on the same stream ahead of the pass
-    for (int b = 0; b < n && e == cudaSuccess; ++b) {
-      const size_t pts = (size_t)scans[b].rings * scans[b].cols;
-      if (!pts) continue;
-      if (!io[b].xyzr || !io[b].elevation || !scans[b].xyzr) return LSG_E_ARG;
-      e = cudaMemcpyAsync(const_cast<float*>(scans[b].xyzr), io[b].xyzr, pts * 16, cudaMemcpyHostToDevice, cs);
-      if (e == cudaSuccess)
-        e = cudaMemcpyAsync(const_cast<float*>(scans[b].elevation), io[b].elevation, sizeof(float) * scans[b].rings,
-                            cudaMemcpyHostToDevice, cs);
-    }
+    for (int b = 0; b < n; ++b)
+      if (scans[b].rings > 0 && scans[b].cols > 0 && (!io[b].xyzr || !io[b].elevation)) return LSG_E_ARG;
+    for (int b = 0; b < n && e == cudaSuccess; ++b) e = copy_in(scans[b], io[b], cs);
     if (e != cudaSuccess) return cuda_status(e);
   }
   ScanDesc* hd = static_cast<ScanDesc*>(sg.host);
@@ -511,16 +571,7 @@ static lsg_status batch_launch(lsg_ctx* ctx, int32_t n, const lsg_scan* scans, c
   if (e == cudaSuccess && t0 > 0) e = launch_flatten(tile, a, cs, true);
   if (io) {
     // results device -> host, behind the pass
-    for (int b = 0; b < n && e == cudaSuccess; ++b) {
-      const size_t pts = (size_t)scans[b].rings * scans[b].cols, nv = (size_t)scans[b].rings * Ws[b];
-      if (io[b].nseg) e = cudaMemcpyAsync(io[b].nseg, outs[b].nseg, sizeof(int32_t), cudaMemcpyDeviceToHost, cs);
-      if (e == cudaSuccess && io[b].labels && pts)
-        e = cudaMemcpyAsync(io[b].labels, outs[b].labels, pts * 4, cudaMemcpyDeviceToHost, cs);
-      if (e == cudaSuccess && io[b].meshbits && nv)
-        e = cudaMemcpyAsync(io[b].meshbits, outs[b].meshbits, nv, cudaMemcpyDeviceToHost, cs);
-      if (e == cudaSuccess && io[b].normals && nv)
-        e = cudaMemcpyAsync(io[b].normals, outs[b].normals, nv * 12, cudaMemcpyDeviceToHost, cs);
-    }
+    for (int b = 0; b < n && e == cudaSuccess; ++b) e = copy_out(scans[b], Ws[b], outs[b], io[b], cs);
   }
   return cuda_status(e);
 }
@@ -599,6 +650,144 @@ static lsg_status plan_layout(lsg_plan* pl, int tile) {
 // Scan groups of the overlapped schedule.
 constexpr int kGroups = 4;
 
+namespace {
+
+// One host<->device copy of a run; consecutive copies whose source and
+// destination both continue the previous one are merged.
+struct Copy {
+  char* dst;
+  const char* src;
+  size_t bytes;
+};
+
+void add_copy(std::vector<Copy>& v, void* dst, const void* src, size_t bytes) {
+  if (!bytes || !dst || !src) return;
+  char* d = static_cast<char*>(dst);
+  const char* s = static_cast<const char*>(src);
+  if (!v.empty() && v.back().dst + v.back().bytes == d && v.back().src + v.back().bytes == s) {
+    v.back().bytes += bytes;
+    return;
+  }
+  v.push_back(Copy{d, s, bytes});
+}
+
+cudaError_t issue(const std::vector<Copy>& v, cudaMemcpyKind kind, cudaStream_t st, size_t& total) {
+  for (const Copy& c : v) {
+    const cudaError_t e = cudaMemcpyAsync(c.dst, c.src, c.bytes, kind, st);
+    if (e != cudaSuccess) return e;
+    total += c.bytes;
+  }
+  return cudaSuccess;
+}
+
+// Chunk boundaries: runs of consecutive scans with about equal point counts.
+std::vector<int> chunk_bounds(const lsg_plan* pl) {
+  std::vector<int64_t> pts(pl->n + 1, 0);
+  for (int b = 0; b < pl->n; ++b) pts[b + 1] = pts[b] + (int64_t)pl->dev_in[b].rings * pl->dev_in[b].cols;
+  const int C = std::max(1, std::min(pl->chunks, pl->n));
+  std::vector<int> bounds{0};
+  for (int c = 1; c < C; ++c) {
+    const int64_t target = pts[pl->n] * c / C;
+    int b = (int)(std::lower_bound(pts.begin(), pts.end(), target) - pts.begin());
+    b = std::max(bounds.back() + 1, std::min(b, pl->n - (C - c)));
+    bounds.push_back(b);
+  }
+  bounds.push_back(pl->n);
+  return bounds;
+}
+
+}  // namespace
+
+// Capture of a host-buffer plan: per chunk of scans, the inputs go host ->
+// device on one branch, the chunk's pass (ring order, tiles, border joins,
+// labels) runs on a second once they have landed, and its outputs go device
+// -> host on a third once the pass is done, so that the copies of the
+// neighbouring chunks, in both directions, run under each chunk's pass.
+static cudaError_t capture_io(lsg_plan* pl, cudaStream_t cs, int& launches) {
+  cudaStream_t s_in = nullptr, s_run = nullptr, s_out = nullptr;
+  std::vector<cudaEvent_t> evs;
+  auto new_event = [&](cudaEvent_t* ev) {
+    const cudaError_t e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) evs.push_back(*ev);
+    return e;
+  };
+  cudaError_t e = cudaStreamCreateWithFlags(&s_in, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s_run, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s_out, cudaStreamNonBlocking);
+  cudaEvent_t fork = nullptr;
+  if (e == cudaSuccess) e = new_event(&fork);
+  if (e == cudaSuccess) e = cudaEventRecord(fork, cs);
+  for (cudaStream_t st : {s_in, s_run, s_out})
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, fork, 0);
+  const std::vector<int> bounds = chunk_bounds(pl);
+  size_t h2d = 0, d2h = 0;
+  launches = 0;
+  for (size_t c = 0; c + 1 < bounds.size() && e == cudaSuccess; ++c) {
+    const int b0 = bounds[c], b1 = bounds[c + 1];
+    std::vector<Copy> in, elev, lab, cnt, mb, nrm;
+    for (int b = b0; b < b1; ++b) {
+      const lsg_scan& sc = pl->dev_in[b];
+      const lsg_host_io& io = pl->io[b];
+      const ScanDesc& d = pl->host_desc[b];
+      const size_t pts = (size_t)d.H * d.W, nv = (size_t)d.H * d.Ws;
+      if (pts) {
+        if (sc.xyzr) add_copy(in, const_cast<float*>(sc.xyzr), io.xyzr, pts * 16);
+        else add_copy(in, const_cast<float*>(sc.range), io.xyzr, pts * 4);
+        add_copy(elev, const_cast<float*>(sc.elevation), io.elevation, sizeof(float) * d.H);
+        add_copy(lab, io.labels, pl->dev_out[b].labels, pts * 4);
+        add_copy(mb, io.meshbits, pl->dev_out[b].meshbits, nv);
+        add_copy(nrm, io.normals, pl->dev_out[b].normals, nv * 12);
+      }
+      add_copy(cnt, io.nseg, pl->dev_out[b].nseg, sizeof(int32_t));
+    }
+    cudaEvent_t ev_in = nullptr, ev_run = nullptr;
+    if (e == cudaSuccess) e = new_event(&ev_in);
+    if (e == cudaSuccess) e = new_event(&ev_run);
+    if (e == cudaSuccess) e = issue(elev, cudaMemcpyHostToDevice, s_in, h2d);
+    if (e == cudaSuccess) e = issue(in, cudaMemcpyHostToDevice, s_in, h2d);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_in, s_in);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s_run, ev_in, 0);
+    // the chunk's pass: ring order over its scans, then its tiles
+    KArgs a;
+    memset(&a, 0, sizeof(a));
+    a.scans = pl->d_desc + b0;
+    a.nscans = b1 - b0;
+    a.err = pl->ctx->d_err;
+    if (e == cudaSuccess) e = launch_prep(a, s_run);
+    ++launches;
+    const int32_t t0 = pl->host_desc[b0].tile0, t1 = b1 < pl->n ? pl->host_desc[b1].tile0 : pl->ntiles;
+    if (t1 > t0) {
+      a.scans = pl->d_desc;
+      a.tile_scan = pl->d_tile_scan;
+      a.nscans = pl->n;
+      a.tile_base = t0;
+      a.ntiles = t1 - t0;
+      if (e == cudaSuccess) e = launch_tile(pl->tile, a, s_run);
+      if (e == cudaSuccess) e = launch_merge(pl->tile, a, s_run);
+      if (e == cudaSuccess) e = launch_flatten(pl->tile, a, s_run);
+      launches += 3;
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(ev_run, s_run);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s_out, ev_run, 0);
+    if (e == cudaSuccess) e = issue(cnt, cudaMemcpyDeviceToHost, s_out, d2h);
+    if (e == cudaSuccess) e = issue(lab, cudaMemcpyDeviceToHost, s_out, d2h);
+    if (e == cudaSuccess) e = issue(mb, cudaMemcpyDeviceToHost, s_out, d2h);
+    if (e == cudaSuccess) e = issue(nrm, cudaMemcpyDeviceToHost, s_out, d2h);
+  }
+  for (cudaStream_t st : {s_in, s_run, s_out}) {
+    cudaEvent_t join = nullptr;
+    if (e == cudaSuccess) e = new_event(&join);
+    if (e == cudaSuccess) e = cudaEventRecord(join, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, join, 0);
+  }
+  pl->h2d_bytes = h2d;
+  pl->d2h_bytes = d2h;
+  for (cudaEvent_t ev : evs) cudaEventDestroy(ev);
+  for (cudaStream_t st : {s_in, s_run, s_out})
+    if (st) cudaStreamDestroy(st);
+  return e;
+}
+
 static lsg_status plan_capture(lsg_plan* pl) {
   if (pl->exec) cudaGraphExecDestroy(pl->exec);
   if (pl->graph) cudaGraphDestroy(pl->graph);
@@ -635,7 +824,13 @@ static lsg_status plan_capture(lsg_plan* pl) {
     // runs one block per scan); the tile kernels see only non-empty scans.
     // Event-record nodes between the phases give per-kernel device times.
     cudaError_t le = cudaEventRecordWithFlags(pl->ev[0], cs, cudaEventRecordExternal);
-    if (pl->fused == 2) {
+    if (pl->chunks > 0) {
+      // host-buffer plan: the copies and passes of every chunk; the phase
+      // events give the whole run's time
+      if (le == cudaSuccess) le = capture_io(pl, cs, launches);
+      for (int k = 1; k < 5 && le == cudaSuccess; ++k)
+        le = cudaEventRecordWithFlags(pl->ev[k], cs, cudaEventRecordExternal);
+    } else if (pl->fused == 2) {
       // scan groups of about equal tile counts, each a chain of the tile,
       // merge and label kernels on its own branch of the graph: as one
       // group's tiles finish, its latency-bound merge and labels run beside
@@ -713,8 +908,8 @@ static lsg_status plan_capture(lsg_plan* pl) {
   return st;
 }
 
-lsg_status lsg_batch_plan(lsg_ctx* ctx, int32_t n, const lsg_scan* scans, const lsg_params* params,
-                          const lsg_out* outs, int tile, lsg_plan** plan) {
+static lsg_status plan_create(lsg_ctx* ctx, int32_t n, const lsg_scan* scans, const lsg_params* params,
+                              const lsg_out* outs, const lsg_host_io* io, int32_t chunks, int tile, lsg_plan** plan) {
   if (!ctx || !plan || n < 1 || !scans || !params || !outs) return LSG_E_ARG;
   *plan = nullptr;
   if (tile == LSG_TILE_AUTO) tile = ctx->tile;
@@ -758,6 +953,13 @@ lsg_status lsg_batch_plan(lsg_ctx* ctx, int32_t n, const lsg_scan* scans, const 
   }
   pl->bytes = bytes;
   ctx->used += bytes;
+  if (io) {
+    pl->chunks = chunks;
+    pl->fused = 0;
+    pl->dev_in.assign(scans, scans + n);
+    pl->dev_out.assign(outs, outs + n);
+    pl->io.assign(io, io + n);
+  }
   lsg_status st = plan_layout(pl, tile);
   if (st == LSG_OK) st = plan_capture(pl);
   if (st != LSG_OK) {
@@ -765,6 +967,45 @@ lsg_status lsg_batch_plan(lsg_ctx* ctx, int32_t n, const lsg_scan* scans, const 
     return st;
   }
   *plan = pl;
+  return LSG_OK;
+}
+
+lsg_status lsg_batch_plan(lsg_ctx* ctx, int32_t n, const lsg_scan* scans, const lsg_params* params,
+                          const lsg_out* outs, int tile, lsg_plan** plan) {
+  return plan_create(ctx, n, scans, params, outs, nullptr, 0, tile, plan);
+}
+
+// Host memory the copies of a host-buffer plan may use: page-locked (or
+// registered) memory, so that they run asynchronously inside the graph.
+static bool pinned_host(const void* p) {
+  if (!p) return true;  // optional outputs may be absent
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeHost;
+}
+
+lsg_status lsg_batch_plan_io(lsg_ctx* ctx, int32_t n, const lsg_scan* scans, const lsg_params* params,
+                             const lsg_out* outs, const lsg_host_io* io, int32_t chunks, int tile, lsg_plan** plan) {
+  if (!ctx || !plan || !io || n < 1 || !scans || chunks < 1) return LSG_E_ARG;
+  *plan = nullptr;
+  DeviceGuard g(ctx->device);
+  for (int b = 0; b < n; ++b) {
+    const bool empty = scans[b].rings == 0 || scans[b].cols == 0;
+    if (!empty && (!io[b].xyzr || !io[b].elevation)) return LSG_E_ARG;
+    if (!pinned_host(io[b].xyzr) || !pinned_host(io[b].elevation) || !pinned_host(io[b].labels) ||
+        !pinned_host(io[b].nseg) || !pinned_host(io[b].meshbits) || !pinned_host(io[b].normals))
+      return LSG_E_ARG;
+  }
+  return plan_create(ctx, n, scans, params, outs, io, chunks, tile, plan);
+}
+
+lsg_status lsg_plan_io_bytes(const lsg_plan* plan, size_t* h2d, size_t* d2h) {
+  if (!plan || plan->chunks == 0) return LSG_E_ARG;
+  if (h2d) *h2d = plan->h2d_bytes;
+  if (d2h) *d2h = plan->d2h_bytes;
   return LSG_OK;
 }
 
@@ -778,6 +1019,7 @@ int lsg_plan_tile(const lsg_plan* plan) { return plan ? plan->tile : -1; }
 
 lsg_status lsg_plan_set_fused(lsg_plan* plan, int fused) {
   if (!plan) return LSG_E_ARG;
+  if (plan->chunks > 0 && fused != 0) return LSG_E_ARG;  // host-buffer plans run phased chunks
   DeviceGuard g(plan->ctx->device);
   plan->fused = (fused == 1 || fused == 2) ? fused : 0;
   return plan_capture(plan);
@@ -806,7 +1048,7 @@ lsg_status lsg_autotune(lsg_plan* plan, int reps, lsg_stream stream, int* best_t
   lsg_status st = LSG_OK;
   // every tile shape under every schedule (one persistent launch, four
   // launches, scan groups on overlapping branches)
-  for (int fused = 2; fused >= 0 && st == LSG_OK; --fused) {
+  for (int fused = plan->chunks > 0 ? 0 : 2; fused >= 0 && st == LSG_OK; --fused) {
     for (int t = 0; t < LSG_TILE_COUNT && st == LSG_OK; ++t) {
       plan->fused = fused;
       st = plan_layout(plan, t);

@@ -89,6 +89,11 @@ def load(build: bool = True):
             "lsg_batch_plan": (ctypes.c_int, [_P, I32, ctypes.POINTER(lsg_scan), ctypes.POINTER(lsg_params),
                                               ctypes.POINTER(lsg_out), ctypes.c_int, ctypes.POINTER(_P)]),
             "lsg_batch_run": (ctypes.c_int, [_P, _P]),
+            "lsg_batch_plan_io": (ctypes.c_int, [_P, I32, ctypes.POINTER(lsg_scan), ctypes.POINTER(lsg_params),
+                                                 ctypes.POINTER(lsg_out), ctypes.POINTER(lsg_host_io), I32,
+                                                 ctypes.c_int, ctypes.POINTER(_P)]),
+            "lsg_plan_io_bytes": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_size_t),
+                                                 ctypes.POINTER(ctypes.c_size_t)]),
             "lsg_batch_launch": (ctypes.c_int, [_P, I32, ctypes.POINTER(lsg_scan), ctypes.POINTER(lsg_params),
                                                 ctypes.POINTER(lsg_out), _P]),
             "lsg_batch_launch_io": (ctypes.c_int, [_P, I32, ctypes.POINTER(lsg_scan), ctypes.POINTER(lsg_params),
@@ -103,6 +108,7 @@ def load(build: bool = True):
             "lsg_plan_phase_times": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float)]),
             "lsg_plan_destroy": (ctypes.c_int, [_P]),
             "lsg_get_error": (ctypes.c_int, [_P]),
+            "lsg_memory_used": (ctypes.c_size_t, [_P]),
             "lsg_selftest_wait_timeout": (ctypes.c_int, [_P]),
             "lsg_segment_stats": (ctypes.c_int, [_P, I32, I32, I32, I32, _P, _P, _P, _P, _P, _P, _P]),
             "lsg_segment_noalloc": (ctypes.c_int, [ctypes.POINTER(lsg_scan), ctypes.POINTER(lsg_params),
@@ -177,6 +183,25 @@ def lsg_batch_plan(ctx: int, scans: Sequence[lsg_scan], params: Sequence[lsg_par
     return h.value
 
 
+def lsg_batch_plan_io(ctx: int, scans: Sequence[lsg_scan], params: Sequence[lsg_params],
+                      outs: Sequence[lsg_out], io: Sequence[lsg_host_io], chunks: int,
+                      tile: int = LSG_TILE_AUTO) -> int:
+    n = len(scans)
+    sa = (lsg_scan * n)(*scans)
+    pa = (lsg_params * n)(*params)
+    oa = (lsg_out * n)(*outs)
+    ia = (lsg_host_io * n)(*io)
+    h = _P()
+    _check(load().lsg_batch_plan_io(ctx, n, sa, pa, oa, ia, int(chunks), tile, ctypes.byref(h)), "lsg_batch_plan_io")
+    return h.value
+
+
+def lsg_plan_io_bytes(plan: int):
+    h2d, d2h = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(load().lsg_plan_io_bytes(plan, ctypes.byref(h2d), ctypes.byref(d2h)), "lsg_plan_io_bytes")
+    return h2d.value, d2h.value
+
+
 def lsg_batch_run(plan: int, stream: int = 0) -> int:
     return load().lsg_batch_run(plan, stream or None)
 
@@ -235,6 +260,11 @@ def lsg_plan_destroy(plan: int) -> None:
 
 def lsg_get_error(ctx: int) -> int:
     return load().lsg_get_error(ctx)
+
+
+def lsg_memory_used(ctx: int) -> int:
+    """Device bytes the context holds (workspace, staging, plans, spins)."""
+    return load().lsg_memory_used(ctx)
 
 
 LSG_NOALLOC_MAX_VERTICES = 1 << 20
@@ -422,6 +452,9 @@ class Context:
     def error(self) -> int:
         return lsg_get_error(self.h)
 
+    def memory_used(self) -> int:
+        return lsg_memory_used(self.h)
+
 
 class Spin:
     """One revolution segmented while its columns arrive (lsg_spin_*): the
@@ -458,13 +491,22 @@ class Spin:
 
 
 class BatchPlan:
-    """A captured batched pass over fixed device buffers."""
+    """A captured batched pass over fixed device buffers; with ``io`` (one
+    lsg_host_io per scan, pinned host buffers) and ``chunks``, the pass from
+    and to host memory (lsg_batch_plan_io)."""
 
     def __init__(self, ctx: Context, scans: List[lsg_scan], params: List[lsg_params], outs: List[lsg_out],
-                 tile: int = LSG_TILE_AUTO):
+                 tile: int = LSG_TILE_AUTO, io: Optional[List[lsg_host_io]] = None, chunks: int = 0):
         self.ctx = ctx
-        self._keep = (scans, params, outs)
-        self.h = lsg_batch_plan(ctx.h, scans, params, outs, tile)
+        self._keep = (scans, params, outs, io)
+        if io is None:
+            self.h = lsg_batch_plan(ctx.h, scans, params, outs, tile)
+        else:
+            self.h = lsg_batch_plan_io(ctx.h, scans, params, outs, io, chunks, tile)
+
+    def io_bytes(self):
+        """(host -> device, device -> host) bytes of one run of a host-buffer plan."""
+        return lsg_plan_io_bytes(self.h)
 
     def run(self, stream=None):
         _check(lsg_batch_run(self.h, _stream_ptr(stream)), "lsg_batch_run")

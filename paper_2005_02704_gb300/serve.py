@@ -34,15 +34,20 @@ from . import lsg
 ShapeKey = Tuple[int, int, int]  # rings, cols, subsample
 
 
+def _block(nbytes: int) -> int:
+    """Bytes the device allocator hands out for a tensor (512-byte blocks)."""
+    return (max(int(nbytes), 1) + 511) // 512 * 512
+
+
 def slot_bytes(key: ShapeKey) -> int:
-    """Device bytes of one slot: inputs, outputs and the request's share of
-    the batch workspace (ring order, sin/cos, union-find parents, tile roots)."""
+    """Device bytes of one slot: its input and output tensors (x,y,z,r,
+    elevations, mesh bytes, normals, labels, segment count).  The pass's
+    workspace belongs to the lanes' contexts, which the server charges to the
+    budget once, up front."""
     H, W, s = key
     Ws = lsg.ws_of(W, s)
-    inputs = H * W * 16 + H * 4
-    outputs = H * Ws * (1 + 12) + H * W * 4 + 4
-    workspace = H * 12 + H * Ws * 4 + H * ((Ws + 7) & ~7) * 2
-    return inputs + outputs + workspace
+    return (_block(H * W * 16) + _block(H * 4) + _block(H * Ws) + _block(H * Ws * 12) + _block(H * W * 4) +
+            _block(4))
 
 
 class SlotPool:
@@ -155,24 +160,39 @@ class Server:
         self.torch = torch
         self.device = torch.device("cuda", device)
         self.max_batch = max_batch
-        self.ctxs = [lsg.Context(device) for _ in range(lanes)]
-        # size every lane's workspace and staging for a full batch of the
-        # largest expected scan, so that serving allocates nothing
+        # every lane's context, with workspace and staging sized for a full
+        # batch of the largest expected scan (so that serving allocates
+        # nothing but slots) and capped at the budget; what they hold is
+        # charged to the budget first, and the slots share the rest
         H, W, s_ = max_shape
         Ws = lsg.ws_of(W, s_)
         tiles = ((H + 3) // 4 + 1) * (Ws // 120 + 1)  # the smallest tile shape: 4 x 120
+        self.ctxs = [lsg.Context(device, budget_bytes=budget_bytes) for _ in range(lanes)]
         for c in self.ctxs:
             lsg.lsg_reserve(c.h, max_batch * lsg.scan_workspace_bytes(H, Ws), max_batch, 2 * max_batch * tiles)
+        self.fixed_bytes = sum(c.memory_used() for c in self.ctxs)
+        if self.fixed_bytes >= budget_bytes:
+            raise ValueError(f"the lanes' workspace ({self.fixed_bytes} bytes) leaves nothing of the budget "
+                             f"{budget_bytes} for scans")
+        self.budget = int(budget_bytes)
+        self.max_shape = max_shape
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(lanes)]
         self.events = [torch.cuda.Event() for _ in range(lanes)]
         self.inflight: List[Optional[List[Request]]] = [None] * lanes
-        self.pool = SlotPool(budget_bytes, lambda k: Slot(k, self.device))
+        self.pool = SlotPool(budget_bytes - self.fixed_bytes, lambda k: Slot(k, self.device))
+        # each lane's argument arrays, filled in place per batch
+        self.c_args = [((lsg.lsg_scan * max_batch)(), (lsg.lsg_params * max_batch)(), (lsg.lsg_out * max_batch)(),
+                        (lsg.lsg_host_io * max_batch)()) for _ in range(lanes)]
         self.pending: collections.deque = collections.deque()
         self.done: List[Request] = []
         self.batches = 0
         self.batch_sizes: List[int] = []
 
     def submit(self, req: Request) -> None:
+        H, W, s_ = req.key
+        Hm, Wm, sm = self.max_shape
+        if H * W > Hm * Wm or H * lsg.ws_of(W, s_) > Hm * lsg.ws_of(Wm, sm) or H > Hm:
+            raise ValueError(f"scan shape {req.key} is larger than the server's largest shape {self.max_shape}")
         self.pending.append(req)
 
     def busy(self) -> bool:
@@ -211,10 +231,7 @@ class Server:
         st = self.streams[k]
         now = time.perf_counter()
         n = len(batch)
-        scans = (lsg.lsg_scan * n)()
-        params = (lsg.lsg_params * n)()
-        outs = (lsg.lsg_out * n)()
-        io = (lsg.lsg_host_io * n)()
+        scans, params, outs, io = self.c_args[k]
         for b, req in enumerate(batch):
             slot = req.slot
             req.t_launch = now
@@ -236,7 +253,7 @@ class Server:
                 h.normals = None
             io[b] = h
         # uploads, the batched pass and the result downloads, on this lane
-        rc = lsg.lsg_batch_launch_io(self.ctxs[k].h, scans, params, outs, io, int(st.cuda_stream))
+        rc = lsg.load().lsg_batch_launch_io(self.ctxs[k].h, n, scans, params, outs, io, int(st.cuda_stream))
         if rc != lsg.LSG_OK:
             raise lsg.LsgError(rc, "lsg_batch_launch_io")
         self.events[k].record(st)
@@ -384,6 +401,11 @@ def _run_serial(feeds: Sequence[SensorFeed], trace, time_scale: float, device: i
     t1 = time.perf_counter()
     ctx.close()
     return summarize(reqs, t1 - t0)
+
+
+def device_footprint(server: Server) -> int:
+    """Device bytes the server holds now: its lanes' contexts and its slots."""
+    return sum(c.memory_used() for c in server.ctxs) + server.pool.used
 
 
 def summarize(reqs: Sequence[Request], wall_s: float) -> dict:

@@ -85,7 +85,8 @@ def test_batch_equals_per_scan(ctx, tile, schedule):
 def test_range_input_batch_equals_per_scan(ctx, schedule):
     """Range-only decoding in a batch (x,y,z from the ring elevation and the
     column azimuth) equals the per-scan range-only path bit for bit, and the
-    chunked host pipeline over range inputs gives the same labels."""
+    host-buffer plan (lsg_batch_plan_io) over range inputs gives the same
+    outputs in host memory."""
     lsg, _ = mods()
     specs = mixed_specs(10, 5600)
     scans = [lidarsim.make_scan(sp) for sp in specs]
@@ -103,14 +104,18 @@ def test_range_input_batch_equals_per_scan(ctx, schedule):
         torch.cuda.synchronize()
         assert torch.equal(out.meshbits, mb) and torch.equal(out.normals, nrm)
         assert torch.equal(out.labels, lab) and torch.equal(out.nseg, nseg)
-    want_lab, want_nseg = db.d_lab.cpu().clone(), db.d_nseg.cpu().clone()
+    want = [t.cpu().clone() for t in (db.d_lab, db.d_nseg, db.d_mb, db.d_nrm)]
     db.d_lab.fill_(-7)
-    pipe = db.pipeline(ctx, chunks=3, schedule=schedule)
-    h2d, d2h = pipe.step()
+    pio = db.plan_io(ctx, chunks=3)
+    pio.run()
     torch.cuda.synchronize()
-    assert h2d == db.points * 4 + db.h_elev.numel() * 4 and d2h == db.points * 4 + db.n * 4
-    assert torch.equal(db.h_lab, want_lab) and torch.equal(db.h_nseg, want_nseg)
-    pipe.close()
+    assert ctx.error() == lsg.LSG_OK
+    h2d, d2h = pio.io_bytes()
+    assert h2d == db.points * 4 + db.h_elev.numel() * 4
+    assert d2h == db.points * 4 + db.n * 4 + db.vertices * 13
+    for got, w in zip((db.h_lab, db.h_nseg, db.h_mb, db.h_nrm), want):
+        assert torch.equal(got, w)
+    pio.close()
     plan.close()
 
 
@@ -168,10 +173,13 @@ def test_bench_workload_512_scans(ctx):
     plan.close()
 
 
-@pytest.mark.parametrize("chunks", [1, 3, 8])
-def test_host_pipeline_equals_plan(ctx, chunks):
-    """The chunked end-to-end host path gives the single plan's labels and
-    segment counts in the pinned host buffers."""
+@pytest.mark.parametrize("chunks", [1, 3, 8, 64])
+def test_host_buffer_plan_equals_plan(ctx, chunks):
+    """The end-to-end plan (lsg_batch_plan_io: host inputs copied in, the pass,
+    every output copied back, in chunks) leaves the device plan's labels,
+    segment counts, mesh bytes and normals in the pinned host buffers, and
+    declares the bytes it moves.  Each of two replays starts from zeroed
+    device inputs and host outputs, so each must copy in both directions."""
     lsg, _ = mods()
     specs = mixed_specs(10, 7000)
     scans = [lidarsim.make_scan(sp) for sp in specs]
@@ -180,21 +188,37 @@ def test_host_pipeline_equals_plan(ctx, chunks):
     plan.set_fused(False)
     plan.run()
     torch.cuda.synchronize()
-    want_lab, want_nseg = db.d_lab.cpu().clone(), db.d_nseg.cpu().clone()
-    db.d_lab.fill_(-7)
-    db.d_nseg.fill_(-7)
-    # chunk plans of one or two scans under the grouped schedule cover
-    # plans with fewer scans than groups
-    pipe = db.pipeline(ctx, lsg.TILES["32x120"], chunks=chunks, schedule=2 if chunks == 8 else 0)
-    assert len(pipe.ranges) == min(chunks, db.n)
-    assert pipe.ranges[0][0] == 0 and pipe.ranges[-1][1] == db.n
-    h2d, d2h = pipe.step()
-    torch.cuda.synchronize()
-    assert ctx.error() == lsg.LSG_OK
-    assert h2d == db.points * 16 + db.h_elev.numel() * 4 and d2h == db.points * 4 + db.n * 4
-    assert torch.equal(db.h_lab, want_lab) and torch.equal(db.h_nseg, want_nseg)
-    pipe.close()
+    want = [t.cpu().clone() for t in (db.d_lab, db.d_nseg, db.d_mb, db.d_nrm)]
+    for t in (db.d_lab, db.d_nseg, db.d_mb, db.d_nrm, db.d_in):
+        t.fill_(0)
+    pio = db.plan_io(ctx, lsg.TILES["32x120"], chunks=chunks)
+    assert pio.launches == 4 * min(chunks, db.n)
+    h2d, d2h = pio.io_bytes()
+    assert h2d == db.points * 16 + db.h_elev.numel() * 4
+    assert d2h == db.points * 4 + db.n * 4 + db.vertices * 13
+    for rep in range(2):
+        db.d_in.fill_(0)
+        torch.cuda.synchronize()
+        for t in (db.h_lab, db.h_nseg, db.h_mb, db.h_nrm):
+            t.fill_(0)
+        pio.run()
+        torch.cuda.synchronize()
+        assert ctx.error() == lsg.LSG_OK
+        for got, w in zip((db.h_lab, db.h_nseg, db.h_mb, db.h_nrm), want):
+            assert torch.equal(got, w), rep
+    pio.close()
     plan.close()
+
+
+def test_host_buffer_plan_rejects_pageable_memory(ctx):
+    lsg, batch = mods()
+    specs = mixed_specs(2, 7100)
+    scans = [lidarsim.make_scan(sp) for sp in specs]
+    shapes = [batch.ScanShape(s.rings, s.cols, sp.subsample) for sp, s in zip(specs, scans)]
+    db = batch.DeviceBatch(shapes, [params_of(sp) for sp in specs], 0, pinned=False)
+    with pytest.raises(lsg.LsgError) as ei:
+        db.plan_io(ctx, chunks=2)
+    assert ei.value.status == lsg.LSG_E_ARG
 
 
 @pytest.mark.parametrize("schedule", [1, 0, 2], ids=["fused", "phased", "grouped"])

@@ -39,16 +39,25 @@ def _check(reqs, feeds, alone):
         assert np.all(np.arctan2(cr, np.sum(a[has] * b[has], axis=1)) <= 1e-4)
 
 
-@pytest.mark.parametrize("budget_mb,lanes,max_batch", [(1024, 3, 16), (40, 2, 4)])
+@pytest.mark.parametrize("budget_mb,lanes,max_batch", [(1024, 3, 16), (60, 2, 4)])
 def test_results_are_the_same_alone_and_in_the_mix(gpu_lib, budget_mb, lanes, max_batch):
     from paper_2005_02704_gb300 import serve
     feeds = serve.make_feeds(lidarsim.sensor_specs(8), scans_per_sensor=2)
     alone = _alone_results(feeds)
     trace = serve.arrival_trace([f.rate_hz for f in feeds], duration_s=3.0, burst=(1.0, 2.0, 4.0), seed=5)
-    server = serve.Server(budget_bytes=budget_mb << 20, lanes=lanes, max_batch=max_batch)
+    budget = budget_mb << 20
+    torch.cuda.synchronize()
+    base = torch.cuda.memory_allocated()
+    torch.cuda.reset_peak_memory_stats()
+    server = serve.Server(budget_bytes=budget, lanes=lanes, max_batch=max_batch)
     stats = serve.run_served(server, feeds, trace, time_scale=10.0, keep_geometry=True)
     assert stats["scans"] == len(trace) == len(server.done)
-    assert server.pool.peak <= budget_mb << 20
+    # the device footprint stays within the budget: the lanes' contexts (which
+    # did not grow) plus the slots, whose tensors are the only torch
+    # allocations the server makes
+    assert sum(c.memory_used() for c in server.ctxs) == server.fixed_bytes
+    assert server.fixed_bytes + server.pool.peak <= budget
+    assert torch.cuda.max_memory_allocated() - base <= server.pool.budget
     assert max(server.batch_sizes) > 1  # scans were batched together
     _check(server.done, feeds, alone)
     server.close()
