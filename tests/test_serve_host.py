@@ -47,10 +47,13 @@ def test_oversized_scan_is_refused():
         pool.acquire((11, 10, 1))
 
 
-def test_slot_bytes_counts_inputs_outputs_and_workspace():
-    H, W, s = 128, 4096, 1
-    assert serve.slot_bytes((H, W, s)) == H * W * 16 + H * 4 + H * W * 13 + H * W * 4 + 4 + H * 12 + H * W * 6
-    assert serve.slot_bytes((3, 5, 1)) == 3 * 5 * 16 + 3 * 4 + 3 * 5 * 17 + 4 + 3 * 12 + 3 * 5 * 4 + 3 * 8 * 2
+def test_slot_bytes_counts_the_slot_tensors_in_allocator_blocks():
+    # a slot holds x,y,z,r, elevations, mesh bytes, normals, labels and the
+    # segment count, each rounded up to 512-byte allocator blocks; the pass's
+    # workspace belongs to the lanes' contexts, not to slots
+    H, W = 128, 4096
+    assert serve.slot_bytes((H, W, 1)) == H * W * 16 + 512 + H * W + H * W * 12 + H * W * 4 + 512
+    assert serve.slot_bytes((3, 5, 1)) == 6 * 512
     assert serve.slot_bytes((64, 2048, 2)) < serve.slot_bytes((64, 2048, 1))
 
 
