@@ -176,9 +176,11 @@ class Server:
                              f"{budget_bytes} for scans")
         self.budget = int(budget_bytes)
         self.max_shape = max_shape
+        self.shapes_ok = set()
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(lanes)]
         self.events = [torch.cuda.Event() for _ in range(lanes)]
         self.inflight: List[Optional[List[Request]]] = [None] * lanes
+        self.n_inflight = 0
         self.pool = SlotPool(budget_bytes - self.fixed_bytes, lambda k: Slot(k, self.device))
         # each lane's argument arrays, filled in place per batch
         self.c_args = [((lsg.lsg_scan * max_batch)(), (lsg.lsg_params * max_batch)(), (lsg.lsg_out * max_batch)(),
@@ -189,16 +191,20 @@ class Server:
         self.batch_sizes: List[int] = []
 
     def submit(self, req: Request) -> None:
-        H, W, s_ = req.key
-        Hm, Wm, sm = self.max_shape
-        if H * W > Hm * Wm or H * lsg.ws_of(W, s_) > Hm * lsg.ws_of(Wm, sm) or H > Hm:
-            raise ValueError(f"scan shape {req.key} is larger than the server's largest shape {self.max_shape}")
+        if req.key not in self.shapes_ok:
+            H, W, s_ = req.key
+            Hm, Wm, sm = self.max_shape
+            if H * W > Hm * Wm or H * lsg.ws_of(W, s_) > Hm * lsg.ws_of(Wm, sm) or H > Hm:
+                raise ValueError(f"scan shape {req.key} is larger than the server's largest shape {self.max_shape}")
+            self.shapes_ok.add(req.key)
         self.pending.append(req)
 
     def busy(self) -> bool:
-        return bool(self.pending) or any(b is not None for b in self.inflight)
+        return bool(self.pending) or self.n_inflight > 0
 
     def _reap(self) -> None:
+        if not self.n_inflight:
+            return
         for k, batch in enumerate(self.inflight):
             if batch is None or not self.events[k].query():
                 continue
@@ -215,6 +221,7 @@ class Server:
                 req.slot = None
                 self.done.append(req)
             self.inflight[k] = None
+            self.n_inflight -= 1
 
     def _launch(self, k: int) -> bool:
         batch: List[Request] = []
@@ -231,6 +238,35 @@ class Server:
         st = self.streams[k]
         now = time.perf_counter()
         n = len(batch)
+        if n == 1:
+            # a batch of one passes the slot's own descriptors by reference
+            req = batch[0]
+            slot = req.slot
+            req.t_launch = now
+            sc = slot.c_scan
+            sc.azimuth0 = req.az0
+            sc.azimuth_step = req.daz
+            h = slot.c_io
+            h.xyzr = req.host_xyzr.data_ptr()
+            h.elevation = req.host_elev.data_ptr()
+            if req.keep_geometry:
+                mbh, nrh = slot.geometry_buffers()
+                h.meshbits = mbh.data_ptr() if mbh.numel() else None
+                h.normals = nrh.data_ptr() if nrh.numel() else None
+            else:
+                h.meshbits = None
+                h.normals = None
+            prm = req.c_params if req.c_params is not None else req.params.to_c()
+            rc = lsg.load().lsg_batch_launch_io(self.ctxs[k].h, 1, ctypes.byref(sc), ctypes.byref(prm),
+                                                ctypes.byref(slot.c_out), ctypes.byref(h), int(st.cuda_stream))
+            if rc != lsg.LSG_OK:
+                raise lsg.LsgError(rc, "lsg_batch_launch_io")
+            self.events[k].record(st)
+            self.inflight[k] = batch
+            self.n_inflight += 1
+            self.batches += 1
+            self.batch_sizes.append(1)
+            return True
         scans, params, outs, io = self.c_args[k]
         for b, req in enumerate(batch):
             slot = req.slot
@@ -258,6 +294,7 @@ class Server:
             raise lsg.LsgError(rc, "lsg_batch_launch_io")
         self.events[k].record(st)
         self.inflight[k] = batch
+        self.n_inflight += 1
         self.batches += 1
         self.batch_sizes.append(n)
         return True
@@ -265,9 +302,10 @@ class Server:
     def poll(self) -> None:
         """Reap finished batches, then launch waiting scans on idle lanes."""
         self._reap()
-        for k in range(len(self.inflight)):
-            if self.inflight[k] is None and self.pending:
-                self._launch(k)
+        if self.pending:
+            for k in range(len(self.inflight)):
+                if self.inflight[k] is None and self.pending:
+                    self._launch(k)
 
     def drain(self) -> None:
         while self.busy():

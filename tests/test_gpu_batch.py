@@ -212,7 +212,7 @@ def test_host_buffer_plan_equals_plan(ctx, chunks):
 
 def test_host_buffer_plan_rejects_pageable_memory(ctx):
     lsg, batch = mods()
-    specs = mixed_specs(2, 7100)
+    specs = lidarsim.batch_specs(2, 7100)
     scans = [lidarsim.make_scan(sp) for sp in specs]
     shapes = [batch.ScanShape(s.rings, s.cols, sp.subsample) for sp, s in zip(specs, scans)]
     db = batch.DeviceBatch(shapes, [params_of(sp) for sp in specs], 0, pinned=False)
