@@ -1088,6 +1088,89 @@ __device__ __forceinline__ int32_t root_label(const int32_t* lab_s, uint32_t r) 
   return r == NO_ROOT ? -1 : lab_s[r];
 }
 
+// Labels of one tile at s = 1, where every point is a mesh vertex: (1) each
+// thread takes quads of the tile's local roots and resolves the global root
+// of every entry that is a tile root itself (up to four union-find chains in
+// flight), storing its label (the root's index) in lab_s; (2) after one
+// barrier, each thread writes the labels of the same quads as 16-byte
+// stores, every entry taking its tile root's label.
+template <int TR, int NW, int NTB, bool CO>
+__device__ __forceinline__ void flatten_s1(const ScanDesc* d, const Loc& L, int32_t* lab_s) {
+  constexpr int TC = NW * SO;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int Ws = L.Ws;
+  const uint16_t* lroot = d->lroot;
+  const int32_t* parent = d->parent;
+  int32_t* __restrict__ labels = d->labels;
+  const int limit = L.H * Ws + 1;
+  const size_t pitch = root_pitch(Ws);
+  const int nq = (L.cn + 3) >> 2, nquad = L.rn * nq;  // quads holding at least one column of the tile
+  auto quad_ptr = [&](int lr, int q) {
+    return reinterpret_cast<const uint2*>(lroot + (size_t)(L.r0 + lr) * pitch + L.c0) + q;
+  };
+  int nroots = 0;
+  for (int k = tid; k < nquad; k += NTB) {
+    const int lr = k / nq, q = k - lr * nq;
+    const uint2 r4 = ld_in<CO>(quad_ptr(lr, q));
+    const int v0 = lr * TC + 4 * q;
+    const uint32_t e[4] = {r4.x & 0xffffu, r4.x >> 16, r4.y & 0xffffu, r4.y >> 16};
+    const int g0 = (L.r0 + lr) * Ws + L.c0 + 4 * q;  // scan index of the quad's first vertex
+    int x[4];
+    bool root[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      // entries past the tile's last column belong to the next tile or the
+      // row padding
+      root[j] = e[j] == (uint32_t)(v0 + j) && 4 * q + j < L.cn;
+      x[j] = g0 + j;
+    }
+    for (int it = 0; it < limit; ++it) {
+      bool more = false;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (!root[j]) continue;
+        const int p = ld_in<CO>(parent + x[j]);
+        if (p != x[j]) {
+          x[j] = p;
+          more = true;
+        }
+      }
+      if (!more) break;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (!root[j]) continue;
+      nroots += x[j] == g0 + j;
+      lab_s[v0 + j] = x[j];  // s = 1: the point index is the vertex index
+    }
+  }
+  const int cnt = __reduce_add_sync(FULL, nroots);
+  if (lane == 0 && cnt) atomicAdd(d->nseg, cnt);
+  __syncthreads();
+  for (int k = tid; k < nquad; k += NTB) {
+    const int lr = k / nq, q = k - lr * nq;
+    const uint2 r4 = ld_in<CO>(quad_ptr(lr, q));
+    const int lc = 4 * q;
+    // entries past the tile's last column (the next tile's, or the row
+    // padding, which nothing writes) are never used as indices
+    const int lim = L.cn - lc;
+    const uint32_t e0 = r4.x & 0xffffu, e1 = lim > 1 ? (r4.x >> 16) : (uint32_t)NO_ROOT;
+    const uint32_t e2 = lim > 2 ? (r4.y & 0xffffu) : (uint32_t)NO_ROOT;
+    const uint32_t e3 = lim > 3 ? (r4.y >> 16) : (uint32_t)NO_ROOT;
+    const int4 o = make_int4(root_label(lab_s, e0), root_label(lab_s, e1), root_label(lab_s, e2),
+                             root_label(lab_s, e3));
+    int32_t* dst = labels + (size_t)(L.r0 + lr) * L.W + L.c0 + lc;
+    if (lc + 4 <= L.cn && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+      *reinterpret_cast<int4*>(dst) = o;
+    } else {
+      dst[0] = o.x;
+      if (lc + 1 < L.cn) dst[1] = o.y;
+      if (lc + 2 < L.cn) dst[2] = o.z;
+      if (lc + 3 < L.cn) dst[3] = o.w;
+    }
+  }
+}
+
 // Labels of one tile (NTB threads; fsm: FlatGeo<TR,NW>::bytes of dynamic
 // shared memory; nlist: a shared counter).
 template <int TR, int NW, int NTB, bool CO = false>
@@ -1100,6 +1183,10 @@ __device__ __forceinline__ void flatten_body(const ScanDesc* d, int lt, unsigned
   uint16_t* list_s = reinterpret_cast<uint16_t*>(fsm + FG::off_list);
   const int tid = threadIdx.x, lane = tid & 31, wf = tid >> 5;
   const Loc L = make_loc(d, lt, TR, TC);
+  if (L.s == 1) {
+    flatten_s1<TR, NW, NTB, CO>(d, L, lab_s);
+    return;
+  }
   const int W = L.W, Ws = L.Ws, s = L.s;
   const uint16_t* lroot = d->lroot;
   const int32_t* parent = d->parent;
