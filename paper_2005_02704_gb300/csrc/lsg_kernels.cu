@@ -144,6 +144,17 @@ __device__ __forceinline__ int find_sh(int* P, int x, int limit) {
   return x;
 }
 
+// Root of x once every union is done (the forest no longer changes): plain
+// loads without path halving, so that independent chains overlap.
+__device__ __forceinline__ int find_done_sh(const int* P, int x, int limit) {
+  int p = P[x];
+  while (p != x && limit-- > 0) {
+    x = p;
+    p = P[x];
+  }
+  return x;
+}
+
 __device__ void union_sh(int* P, int a, int b, int limit, int32_t* err) {
   for (int it = 0; it < limit; ++it) {
     a = find_sh(P, a, limit);
@@ -816,8 +827,8 @@ __device__ __forceinline__ void tile_cross_and_roots(const Loc& L, const uint8_t
     const int posA = (int)(ps & 0xffu), posB = (int)(ps >> 8);
     const int vA = lr * TC + lcA;
     int rA = 0, rB = 0;
-    if (act && posA == 2 * lane) rA = find_sh(lp, vA, G::NV + 1);
-    if (act && posB == 2 * lane + 1) rB = find_sh(lp, vA + 1, G::NV + 1);
+    if (act && posA == 2 * lane) rA = find_done_sh(lp, vA, G::NV + 1);
+    if (act && posB == 2 * lane + 1) rB = find_done_sh(lp, vA + 1, G::NV + 1);
     const uint32_t pub = (uint32_t)rA | ((uint32_t)rB << 16);
     const uint32_t gA = __shfl_sync(FULL, pub, posA >> 1), gB = __shfl_sync(FULL, pub, posB >> 1);
     if (act && lcA < L.cn) {
