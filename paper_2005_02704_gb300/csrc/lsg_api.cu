@@ -208,7 +208,8 @@ int ctx_tile(const lsg_ctx* ctx, const int* H, const int* Ws, int n) {
   return ctx->tile >= 0 ? ctx->tile : pick_tile(H, Ws, n, ctx->sms);
 }
 
-lsg_status run_pass(const KArgs& a, int tile, bool geometry, cudaStream_t st) {
+lsg_status run_pass(KArgs a, int tile, bool geometry, cudaStream_t st) {
+  a.s1_only = a.one.s == 1;
   // the three kernels after k_prep start while their predecessor drains
   cudaError_t e = launch_prep(a, st);
   if (e == cudaSuccess) e = geometry ? launch_tile(tile, a, st, true) : launch_tile_ccl(tile, a, st, true);
@@ -358,6 +359,7 @@ lsg_status lsg_label_from_mask(lsg_ctx* ctx, int32_t H, int32_t W, int32_t s, in
   a.ntiles = d.tiles_r * d.tiles_c;
   a.nscans = 1;
   a.err = ctx->d_err;
+  a.s1_only = s == 1;
   // no elevations: the ring order is the identity and only nseg is reset
   cudaError_t e = cudaMemsetAsync(nseg, 0, sizeof(int32_t), cs);
   if (e == cudaSuccess) e = launch_tile_ccl(tile, a, cs);
@@ -565,6 +567,9 @@ static lsg_status batch_launch(lsg_ctx* ctx, int32_t n, const lsg_scan* scans, c
   a.ntiles = t0;
   a.nscans = n;
   a.err = ctx->d_err;
+  a.s1_only = 1;
+  for (int b = 0; b < n; ++b)
+    if (params[b].subsample != 1) a.s1_only = 0;
   e = launch_prep(a, cs);
   if (e == cudaSuccess && t0 > 0) e = launch_tile(tile, a, cs, true);
   if (e == cudaSuccess && t0 > 0) e = launch_merge(tile, a, cs, true);
@@ -698,6 +703,13 @@ std::vector<int> chunk_bounds(const lsg_plan* pl) {
 
 }  // namespace
 
+// Do the plan's scans [b0, b1) all have s = 1?
+static int plan_s1_only(const lsg_plan* pl, int b0, int b1) {
+  for (int b = b0; b < b1; ++b)
+    if (pl->host_desc[b].s != 1) return 0;
+  return 1;
+}
+
 // Capture of a host-buffer plan: per chunk of scans, the inputs go host ->
 // device on one branch, the chunk's pass (ring order, tiles, border joins,
 // labels) runs on a second once they have landed, and its outputs go device
@@ -753,6 +765,7 @@ static cudaError_t capture_io(lsg_plan* pl, cudaStream_t cs, int& launches) {
     a.scans = pl->d_desc + b0;
     a.nscans = b1 - b0;
     a.err = pl->ctx->d_err;
+    a.s1_only = plan_s1_only(pl, b0, b1);
     if (e == cudaSuccess) e = launch_prep(a, s_run);
     ++launches;
     const int32_t t0 = pl->host_desc[b0].tile0, t1 = b1 < pl->n ? pl->host_desc[b1].tile0 : pl->ntiles;
@@ -803,6 +816,7 @@ static lsg_status plan_capture(lsg_plan* pl) {
   a.ntiles = pl->ntiles;
   a.nscans = pl->n;
   a.err = pl->ctx->d_err;
+  a.s1_only = plan_s1_only(pl, 0, pl->n);
   for (int k = 0; k < 5 && e == cudaSuccess; ++k)
     if (!pl->ev[k]) e = cudaEventCreate(&pl->ev[k]);
   // side streams and fork / join events of the grouped schedule
@@ -1158,6 +1172,7 @@ lsg_status lsg_spin_begin(lsg_ctx* ctx, const lsg_scan* scan, const lsg_params* 
   set_tiles(sp->a.one, sp->tile, 0);
   sp->a.nscans = 1;
   sp->a.err = ctx->d_err;
+  sp->a.s1_only = params->subsample == 1;
   ScanDesc& d = sp->a.one;
   if (scan->rings == 0 || scan->cols == 0) {
     const cudaError_t e = cudaMemsetAsync(out->nseg, 0, sizeof(int32_t), cs);

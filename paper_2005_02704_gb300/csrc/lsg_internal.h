@@ -45,6 +45,8 @@ struct KArgs {
   int32_t tile_base;         // batched: first entry of tile_scan this launch covers
   int32_t nscans;
   int32_t* err;              // device error word
+  int32_t s1_only;           // 1: every scan of the launch has s = 1 (the label
+                             // kernel then needs less shared memory)
   ScanDesc one;
 };
 
@@ -63,7 +65,7 @@ struct FusedArgs {
 };
 
 // Device error codes (sticky, OR-ed into *err).
-enum : int32_t { DERR_NAN_ELEV = 1, DERR_TIMEOUT = 2 };
+enum : int32_t { DERR_NAN_ELEV = 1, DERR_TIMEOUT = 2, DERR_LAUNCH = 4 };
 
 struct TileShape {
   int rows, cols;

@@ -55,6 +55,8 @@ constexpr uint16_t NO_ROOT = 0xFFFF;  // tile-local root of a vertex out of rang
 // that a tile's rows can be read with aligned vector loads.
 __host__ __device__ __forceinline__ int root_pitch(int Ws) { return (Ws + 7) & ~7; }
 
+__host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) / 16 * 16; }
+
 TileShape tile_shape(int tile) {
   switch (tile) {
     case LSG_TILE_32x120: return {32, 120};
@@ -1045,7 +1047,7 @@ __global__ void __launch_bounds__(nt_merge<TR, NW>()) k_merge(const __grid_const
 // ---------------------------------------------------------------------------
 // k_flatten: labels, back-fill, segment count
 // ---------------------------------------------------------------------------
-constexpr int NT_FLAT = 256;
+constexpr int NT_FLAT = 128;
 
 // Root of a chain in the (now read-only) global union-find.
 template <bool CO>
@@ -1089,10 +1091,12 @@ template <int TR, int NW>
 struct FlatGeo {
   static constexpr int TC = NW * SO, NV = TR * TC;
   static constexpr int NQ = TC / 4;                                         // root quads per tile row
-  static constexpr size_t off_lr = 0;                                      // uint16 [NV] tile roots
-  static constexpr size_t off_lab = ((sizeof(uint16_t) * NV + 15) / 16) * 16;  // int32 [NV] root labels
-  static constexpr size_t off_list = off_lab + sizeof(int32_t) * NV;       // uint16 [NV] list of roots
-  static constexpr size_t bytes = off_list + ((sizeof(uint16_t) * NV + 15) / 16) * 16;
+  static constexpr size_t off_lab = 0;                                      // int32 [NV] root labels
+  static constexpr size_t off_lr = align16(sizeof(int32_t) * NV);          // uint16 [NV] tile roots
+  static constexpr size_t off_list = off_lr + align16(sizeof(uint16_t) * NV);  // uint16 [NV] list of roots
+  static constexpr size_t bytes = off_list + align16(sizeof(uint16_t) * NV);
+  // launches whose scans all have s = 1 use the root labels alone
+  static constexpr size_t s1_bytes = align16(sizeof(int32_t) * NV);
 };
 
 __device__ __forceinline__ int32_t root_label(const int32_t* lab_s, uint32_t r) {
@@ -1185,7 +1189,8 @@ __device__ __forceinline__ void flatten_s1(const ScanDesc* d, const Loc& L, int3
 // Labels of one tile (NTB threads; fsm: FlatGeo<TR,NW>::bytes of dynamic
 // shared memory; nlist: a shared counter).
 template <int TR, int NW, int NTB, bool CO = false>
-__device__ __forceinline__ void flatten_body(const ScanDesc* d, int lt, unsigned char* fsm, int& nlist) {
+__device__ __forceinline__ void flatten_body(const ScanDesc* d, int lt, unsigned char* fsm, int& nlist,
+                                             bool s1_smem = false, int32_t* err = nullptr) {
   using FG = FlatGeo<TR, NW>;
   constexpr int TC = FG::TC, NQ = FG::NQ, NWF = NTB / 32;
   static_assert(TC % 4 == 0, "tile rows are read as quads of roots");
@@ -1196,6 +1201,10 @@ __device__ __forceinline__ void flatten_body(const ScanDesc* d, int lt, unsigned
   const Loc L = make_loc(d, lt, TR, TC);
   if (L.s == 1) {
     flatten_s1<TR, NW, NTB, CO>(d, L, lab_s);
+    return;
+  }
+  if (s1_smem) {  // launched with the s = 1 shared memory only: refuse the scan
+    if (threadIdx.x == 0 && err) atomicOr(err, DERR_LAUNCH);
     return;
   }
   const int W = L.W, Ws = L.Ws, s = L.s;
@@ -1360,13 +1369,15 @@ __device__ __forceinline__ void flatten_body(const ScanDesc* d, int lt, unsigned
   }
 }
 
-// CTAs of k_flatten per SM: as many as the shared memory holds, at most six
-// (the phases wait on loads, so resident tiles hide each other's latency;
-// six leaves 40 registers a thread).
+// CTAs of k_flatten per SM: as many as the shared memory of an s = 1 launch
+// holds, at most twelve of 128 threads (the phases wait on loads, so resident
+// tiles hide each other's latency; twelve leaves 40 registers a thread, and a
+// CTA fits in what one tile-kernel CTA frees, so that the label work of one
+// scan group interleaves with the tile work of the next).
 template <int TR, int NW>
 constexpr int flat_min_blocks() {
-  constexpr int n = (int)((220u * 1024u) / FlatGeo<TR, NW>::bytes);
-  return n < 1 ? 1 : (n > 6 ? 6 : n);
+  constexpr int n = (int)((220u * 1024u) / FlatGeo<TR, NW>::s1_bytes);
+  return n < 1 ? 1 : (n > 12 ? 12 : n);
 }
 
 template <int TR, int NW>
@@ -1377,7 +1388,7 @@ __global__ void __launch_bounds__(NT_FLAT, (flat_min_blocks<TR, NW>())) k_flatte
   for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
     int lt;
     const ScanDesc* d = tile_desc(a, t, lt);
-    flatten_body<TR, NW, NT_FLAT>(d, lt, fsm, nlist);
+    flatten_body<TR, NW, NT_FLAT>(d, lt, fsm, nlist, a.s1_only != 0, a.err);
     __syncthreads();
   }
 }
@@ -1540,7 +1551,8 @@ static cudaError_t run_merge(const KArgs& a, cudaStream_t st, bool pdl) {
 }
 template <int TR, int NW>
 static cudaError_t run_flatten(const KArgs& a, cudaStream_t st, bool pdl) {
-  return launch_k(k_flatten<TR, NW>, a.ntiles, NT_FLAT, FlatGeo<TR, NW>::bytes, st, pdl, a);
+  return launch_k(k_flatten<TR, NW>, a.ntiles, NT_FLAT,
+                  a.s1_only ? FlatGeo<TR, NW>::s1_bytes : FlatGeo<TR, NW>::bytes, st, pdl, a);
 }
 
 template <int TR, int NW>

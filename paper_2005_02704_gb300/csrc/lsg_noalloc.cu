@@ -90,6 +90,7 @@ extern "C" lsg_status lsg_segment_noalloc(const lsg_scan* scan, const lsg_params
   a.ntiles = a.one.tiles_r * a.one.tiles_c;
   a.nscans = 1;
   a.err = reinterpret_cast<int32_t*>(base + kErrOff);
+  a.s1_only = a.one.s == 1;
   // The error word accumulates flags with atomicOr, so it must start at zero;
   // everything else is fully written by the kernels before it is read.
   cudaError_t e = cudaMemsetAsync(a.err, 0, sizeof(int32_t), cs);
