@@ -163,11 +163,12 @@ SCHEDULES = {0: "phased (4 launches)", 1: "fused (one persistent launch)",
              2: "grouped (ring order, then 4 scan groups of tile / merge / label launches on parallel graph branches)"}
 
 
-def profiled_traffic(kernel: str):
-    """DRAM bytes per point of the kernel from its committed ncu summary,
-    valid only while the kernel source is unchanged since the capture."""
+def profiled_values(profile: str):
+    """The machine-readable lines (- key: `value`) of a committed ncu summary
+    under profiles/, or None when the kernel source has changed since the
+    capture (the summary's kernel_source_sha256 no longer matches)."""
     src = os.path.join(ROOT, "paper_2005_02704_gb300", "csrc", "lsg_kernels.cu")
-    prof = os.path.join(ROOT, "profiles", f"{kernel}_batch512.md")
+    prof = os.path.join(ROOT, "profiles", profile)
     try:
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
         vals = {}
@@ -177,8 +178,18 @@ def profiled_traffic(kernel: str):
                 vals[k.strip()] = v.strip().strip("`")
         if vals.get("kernel_source_sha256") != sha:
             return None
-        return float(vals["dram_bytes_per_point"])
+        return vals
     except Exception:
+        return None
+
+
+def profiled_traffic(kernel: str):
+    """DRAM bytes per point of the kernel from its committed ncu summary,
+    valid only while the kernel source is unchanged since the capture."""
+    vals = profiled_values(f"{kernel}_batch512.md")
+    try:
+        return float(vals["dram_bytes_per_point"]) if vals else None
+    except (KeyError, ValueError):
         return None
 
 
@@ -403,6 +414,17 @@ def single_scan_measurement(local, peak, reps=100, warm=10):
     ctx.close()
     res["note"] = (f"{reps} back-to-back lsg_segment calls per scan after {warm} warm-up calls, tile shape per call; "
                    "L2-resident (latency-bound, not HBM-bound)")
+    # the L2 side of the largest single scan, from the committed one-kernel
+    # ncu capture of its tile kernel (null once the kernels have changed)
+    vals = profiled_values("single_scan_k_tile.md")
+    if vals:
+        try:
+            res["ring128x4096"]["k_tile_l2_frac"] = float(vals["lts_throughput_frac"])
+            res["ring128x4096"]["k_tile_sm_frac"] = float(vals["sm_throughput_frac"])
+            res["ring128x4096"]["k_tile_l2_bytes"] = float(vals["lts_bytes"])
+            res["ring128x4096"]["l2_source"] = "profiles/single_scan_k_tile.md (ncu, lts__throughput and sm__throughput)"
+        except (KeyError, ValueError):
+            pass
     return res
 
 
