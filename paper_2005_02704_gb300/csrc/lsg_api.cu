@@ -889,6 +889,7 @@ static lsg_status plan_capture(lsg_plan* pl) {
       f.nscans = pl->n;
       f.counters = pl->d_counters;
       f.err = pl->ctx->d_err;
+      f.s1_only = plan_s1_only(pl, 0, pl->n);
       if (le == cudaSuccess) le = cudaMemsetAsync(pl->d_counters, 0, sizeof(int32_t) * (1 + 3 * (size_t)pl->n), cs);
       if (le == cudaSuccess) le = cudaEventRecordWithFlags(pl->ev[1], cs, cudaEventRecordExternal);
       if (le == cudaSuccess) le = launch_fused(pl->tile, f, cs);

@@ -62,6 +62,7 @@ struct FusedArgs {
   int32_t nscans;
   int32_t* counters;      // [0] next item, then per scan: rings done, tiles done, merges done
   int32_t* err;
+  int32_t s1_only;        // 1: every scan has s = 1 (less shared memory per CTA)
 };
 
 // Device error codes (sticky, OR-ed into *err).

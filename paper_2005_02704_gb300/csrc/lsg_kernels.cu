@@ -1420,8 +1420,11 @@ __global__ void k_wait_probe(const int32_t* cnt, int32_t* err, unsigned limit) {
 template <int TR, int NW>
 struct FusedGeo {
   static constexpr size_t a = Geo<TR, NW>::bytes, b = FlatGeo<TR, NW>::bytes, c = sizeof(float) * LSG_MAX_RINGS;
-  static constexpr size_t ab = a > b ? a : b;
+  static constexpr size_t b1 = FlatGeo<TR, NW>::s1_bytes;
+  static constexpr size_t ab = a > b ? a : b, ab1 = a > b1 ? a : b1;
   static constexpr size_t bytes = ab > c ? ab : c;
+  // plans whose scans all have s = 1: the labels items need the root labels only
+  static constexpr size_t s1_bytes = ab1 > c ? ab1 : c;
 };
 
 // Every CTA takes the next item of the schedule (one atomic per item), waits
@@ -1457,7 +1460,7 @@ __global__ void __launch_bounds__(NW * 32) k_fused(const __grid_constant__ Fused
     if (ph == PH_PREP) prep_body<NTB>(d, reinterpret_cast<float*>(smem), f.err);
     else if (ph == PH_TILE) tile_body<TR, NW, true>(d, lt, smem, f.err);
     else if (ph == PH_MERGE) merge_body<TR, NW, NTB, true>(d, lt, f.err);
-    else flatten_body<TR, NW, NTB, true>(d, lt, smem, nlist);
+    else flatten_body<TR, NW, NTB, true>(d, lt, smem, nlist, f.s1_only != 0, f.err);
     __syncthreads();
     if (threadIdx.x == 0 && ph != PH_FLAT) {
       __threadfence();  // this CTA's writes before the count that releases them
@@ -1560,11 +1563,11 @@ static cudaError_t run_fused(const FusedArgs& f, cudaStream_t st) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<TR, NW>, NW * 32, FusedGeo<TR, NW>::bytes);
+  const size_t smem = f.s1_only ? FusedGeo<TR, NW>::s1_bytes : FusedGeo<TR, NW>::bytes;
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<TR, NW>, NW * 32, smem);
   if (e != cudaSuccess) return e;
   const int grid = max(1, min(sms * max(per_sm, 1), f.nitems));
-  k_fused<TR, NW><<<grid, NW * 32, FusedGeo<TR, NW>::bytes, st>>>(f);
+  k_fused<TR, NW><<<grid, NW * 32, smem, st>>>(f);
   return cudaGetLastError();
 }
 
