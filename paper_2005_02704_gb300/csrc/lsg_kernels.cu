@@ -267,8 +267,10 @@ struct Geo {
   static constexpr size_t off_ring = 0;
   static constexpr size_t off_lp = 0;
   static constexpr size_t off_tb = ((ring_bytes > lp_bytes ? ring_bytes : lp_bytes) + 15) / 16 * 16;
-  static constexpr size_t off_rows = off_tb + ((NV + 15) / 16) * 16;  // long long [HR] input row offsets
-  static constexpr size_t off_trig = off_rows + ((sizeof(long long) * HR + 15) / 16) * 16;  // float2 [HR] sin, cos
+  // input row offsets long long [HR + RING - 1] (the last RING - 1 entries:
+  // rows past the sweep, never read), then float2 [HR] sin, cos
+  static constexpr size_t off_rows = off_tb + ((NV + 15) / 16) * 16;
+  static constexpr size_t off_trig = off_rows + ((sizeof(long long) * (HR + RING - 1) + 15) / 16) * 16;
   static constexpr size_t off_q = off_trig + ((sizeof(float2) * HR + 15) / 16) * 16;  // uint32 [NW][QCAP]
   // queue uint32 [NW][QCAP], then the run starts of every strip row uint16 [NW][TR][32]
   static constexpr size_t q_bytes = sizeof(uint32_t) * NW * QCAP + sizeof(uint16_t) * NW * TR * 32;
@@ -286,21 +288,22 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // Issue the asynchronous copy of one point into a ring slot: x,y,z,r
 // (16 bytes), or the range alone (4 bytes, into the slot's r; the sweep
 // decodes x,y,z when it reads the slot).  ro = offset of the input row (ring
-// order * W), or -1 when the row is outside the scan: the slot then holds an
-// absent point (r = -1).
+// order * W), or -1 when the row is outside the scan (or past the sweep);
+// then, and for a column outside the scan, the copy reads nothing and fills
+// the slot with zeros: an absent point (r = 0 is out of range, r_min >= 0).
+// No branch: the copy's source size is 0 or the full size.
 __device__ __forceinline__ void fetch_point(float4* slot, const float4* __restrict__ xyzr,
                                             const float* __restrict__ range, long long ro, bool colok,
                                             unsigned coff) {
-  if (colok && ro >= 0) {
-    const size_t o = (size_t)ro + coff;
-    const unsigned dst = (unsigned)__cvta_generic_to_shared(slot);
-    if (xyzr)
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(xyzr + o) : "memory");
-    else
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst + 12u), "l"(range + o) : "memory");
-    return;
-  }
-  *slot = make_float4(0.f, 0.f, 0.f, -1.f);
+  const bool ok = colok && ro >= 0;
+  const size_t o = ok ? (size_t)ro + coff : 0;
+  const unsigned dst = (unsigned)__cvta_generic_to_shared(slot);
+  if (xyzr)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(xyzr + o), "r"(ok ? 16u : 0u)
+                 : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst + 12u), "l"(range + o), "r"(ok ? 4u : 0u)
+                 : "memory");
 }
 
 // Everything of a descriptor the tile kernels use, in registers.
@@ -489,7 +492,7 @@ __device__ __forceinline__ void tile_sweep(const ScanDesc* __restrict__ d, const
 
   const float2 Z2 = make_float2(0.f, 0.f);
   const float QNAN = __int_as_float(0x7fc00000);
-  float2 ppx = Z2, ppy = Z2, ppz = Z2, ppr = make_float2(-1.f, -1.f);  // row k-1 (zeroed out of range)
+  float2 ppx = Z2, ppy = Z2, ppz = Z2, ppr = Z2;  // row k-1 (zeroed out of range)
   float2 rx1 = Z2, ry1 = Z2, rz1 = Z2, lr1 = Z2;                        // R edges of row k-1
   float2 er1 = Z2;                                                      // their existence (0 / 1)
   float2 ux = Z2, uy = Z2, uz = Z2;                // row k-1's normal sums: the terms above it
@@ -509,7 +512,7 @@ __device__ __forceinline__ void tile_sweep(const ScanDesc* __restrict__ d, const
       PB = make_float4(rcB * cpB, rcB * spB, PB.w * te.x, PB.w);
     }
     // refill the slot read one step ago with row hr+RING-1
-    if (hr + RING - 1 < nsteps) fetch(hr + RING - 1, hr + RING - 1);
+    fetch(hr + RING - 1, hr + RING - 1);  // past the sweep: an absent row, nothing read
     cp_async_commit();
 
     const bool vA = in_range(PA.w, rmin, rmax), vB = in_range(PB.w, rmin, rmax);
@@ -601,8 +604,8 @@ __device__ __forceinline__ void tile_sweep(const ScanDesc* __restrict__ d, const
       const uint32_t m2h = m2 | ((m2 & hm) << 3);
       const uint32_t m2A = m2 & 0xffu, m2B = m2 >> 8;
       const uint32_t bA = m2h & 0xffu, bB = m2h >> 8;
-      const int lr = hr - 3;
-      if (lr < L.rn) {
+      const int lr = hr - 3;  // < L.rn: the sweep ends at row r0 + rn + 1
+      {
         if (strip)
           *reinterpret_cast<uint16_t*>(tb + lr * TC + lcA) =
               (uint16_t)((outA ? bA : 0u) | (outB ? bB << 8 : 0u));
@@ -857,17 +860,17 @@ __device__ __forceinline__ void tile_body(const ScanDesc* d, int lt, unsigned ch
   // for range-only input, their elevations' sine and cosine
   long long* rows_s = reinterpret_cast<long long*>(smem + G::off_rows);
   float2* trig_s = reinterpret_cast<float2*>(smem + G::off_trig);
-  for (int k = threadIdx.x; k < L.rn + 3; k += G::NT) {
+  for (int k = threadIdx.x; k < L.rn + 3 + RING - 1; k += G::NT) {
     const int i = L.r0 - 1 + k;
     long long ro = -1;
     float2 te = make_float2(0.f, 1.f);
-    if (i >= 0 && i < L.H) {
+    if (i >= 0 && i < L.H && k < L.rn + 3) {
       const int row = ld_in<CO>(d->order + i);
       if ((unsigned)row < (unsigned)L.H) ro = (long long)row * L.W;
       if (!d->xyzr) te = ld_in<CO>(d->trig + i);
     }
     rows_s[k] = ro;
-    trig_s[k] = te;
+    if (k < L.rn + 3) trig_s[k] = te;  // trig_s has the sweep's rows only
   }
   __syncthreads();
   const bool angle = d->pred == LSG_PRED_ANGLE;
