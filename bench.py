@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--no-single", action="store_true", help="skip the single-scan latency measurement")
     ap.add_argument("--no-range-input", action="store_true", help="skip the range-only input measurement")
     ap.add_argument("--no-accuracy", action="store_true", help="skip the Table-2 accuracy protocol")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) measurements")
+    ap.add_argument("--no-schedules", action="store_true", help="skip timing every schedule of the plan")
     ap.add_argument("--single-only", action="store_true",
                     help="only the single-scan latency measurement (one JSON object; for profiling the per-call path)")
     ap.add_argument("--phased", action="store_true", help="force four phased launches (else the autotuner's choice)")
@@ -587,7 +589,7 @@ def main():
     # ---- every schedule of the same plan and tile shape --------------------
     #      (K replays each, events on the launching stream)
     sched_ms = {}
-    for sch, nm in ((0, "phased"), (1, "fused"), (2, "grouped")):
+    for sch, nm in (() if args.no_schedules else ((0, "phased"), (1, "fused"), (2, "grouped"))):
         plan.set_schedule(sch)
         for _ in range(3):
             plan.run()
@@ -672,16 +674,29 @@ def main():
                 ts.append(e0.elapsed_time(e1))
         return statistics.median(ts)
 
-    plan_io = db.plan_io(ctx, plan.tile, chunks=args.e2e_chunks)
-    h2d, d2h = plan_io.io_bytes()
-    ms_e2e, regions = time_e2e(plan_io)
-    e2e_value = pts_all / (ms_e2e / 1e3)
-    e2e_launches = plan_io.launches
-    plan_io.close()
-    plan_io1 = db.plan_io(ctx, plan.tile, chunks=1)
-    ms_e2e_serial, _ = time_e2e(plan_io1)
-    plan_io1.close()
-    ms_floor = max_over_ranks(link_floor(db))
+    e2e = None
+    if not args.no_e2e:
+        plan_io = db.plan_io(ctx, plan.tile, chunks=args.e2e_chunks)
+        h2d, d2h = plan_io.io_bytes()
+        ms_e2e, regions = time_e2e(plan_io)
+        e2e_launches = plan_io.launches
+        plan_io.close()
+        plan_io1 = db.plan_io(ctx, plan.tile, chunks=1)
+        ms_e2e_serial, _ = time_e2e(plan_io1)
+        plan_io1.close()
+        ms_floor = max_over_ranks(link_floor(db))
+        e2e = {"value": pts_all / (ms_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e,
+               "path": f"lsg_batch_plan_io + lsg_batch_run (C ABI) from pinned host buffers, "
+                       f"{args.e2e_chunks} chunks in one graph: x,y,z,r and elevations in; labels, segment "
+                       "counts, mesh bytes and normals out",
+               "ms_per_step_regions": regions, "gpu_launches_per_step": e2e_launches,
+               "serial_ms_per_step": ms_e2e_serial,
+               "serial_value": pts_all / (ms_e2e_serial / 1e3),
+               "serial_path": "the same plan with one chunk (copy in, pass, copy out in sequence)",
+               "link_floor_ms": ms_floor,
+               "link_floor_note": "the same bytes copied host->device and device->host on two streams at "
+                                  "once, nothing else (torch copies of the pinned mirrors)"}
     # the device plan's outputs again (the host-buffer replays rewrote them)
     plan.run()
     torch.cuda.synchronize()
@@ -690,7 +705,7 @@ def main():
     #     x,y,z decoded on the GPU from the ring elevation and column azimuth:
     #     a quarter of the input bytes, on the device and over the host link
     range_input = None
-    if not args.no_range_input:
+    if not args.no_range_input and not args.no_e2e:
         dbr = batch.DeviceBatch(shapes, [seg_params(sp) for sp in specs], local, form="range")
         for b, s_ in enumerate(scans):
             dbr.set_scan(b, s_)
@@ -841,18 +856,7 @@ def main():
             "kernel_ms": ({"counter_reset": phase[0], "fused": phase[1]} if fused else
                           {"ring_order": phase[0], "tile": phase[1], "merge": phase[2], "labels": phase[3]}),
             "cpu_baseline": cpu,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "ms_per_step": ms_e2e,
-                    "path": f"lsg_batch_plan_io + lsg_batch_run (C ABI) from pinned host buffers, "
-                            f"{args.e2e_chunks} chunks in one graph: x,y,z,r and elevations in; labels, segment "
-                            "counts, mesh bytes and normals out",
-                    "ms_per_step_regions": regions, "gpu_launches_per_step": e2e_launches,
-                    "serial_ms_per_step": ms_e2e_serial,
-                    "serial_value": pts_all / (ms_e2e_serial / 1e3),
-                    "serial_path": "the same plan with one chunk (copy in, pass, copy out in sequence)",
-                    "link_floor_ms": ms_floor,
-                    "link_floor_note": "the same bytes copied host->device and device->host on two streams at "
-                                       "once, nothing else (torch copies of the pinned mirrors)"},
+            "e2e": e2e,
             "batched_latency": batched_latency,
             "range_input": range_input,
             "plain": plain,
