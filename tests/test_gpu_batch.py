@@ -146,7 +146,9 @@ def test_bench_workload_512_scans(ctx):
     specs = lidarsim.batch_specs(512)
     scans = [lidarsim.make_scan(sp) for sp in specs]
     db = make_batch(specs, scans)
-    plan = db.plan(ctx)
+    plan = db.plan(ctx, lsg.TILES["32x120"])
+    plan.set_schedule(2)  # the autotuner's choice for this batch: grouped, 32 x 120 tiles
+    assert plan.tile == lsg.TILES["32x120"] and plan.schedule == 2
     plan.run()
     torch.cuda.synchronize()
     assert ctx.error() == lsg.LSG_OK
