@@ -1127,12 +1127,29 @@ __device__ __forceinline__ void flatten_s1(const ScanDesc* d, const Loc& L, int3
     return reinterpret_cast<const uint2*>(lroot + (size_t)(L.r0 + lr) * pitch + L.c0) + q;
   };
   int nroots = 0;
+  // the quad's four union-find entries are loaded with its roots, so that a
+  // root that no border join moved needs no second round trip (entries of
+  // vertices that are not roots are read and dropped; a row's last quad
+  // reads at most three entries past the scan's parent array, into the
+  // scan's own tile-root array, which follows it in the workspace)
+  const bool vec = (Ws & 3) == 0;  // the quads' entries are 16-byte aligned
   for (int k = tid; k < nquad; k += NTB) {
     const int lr = k / nq, q = k - lr * nq;
+    const int g0 = (L.r0 + lr) * Ws + L.c0 + 4 * q;  // scan index of the quad's first vertex
     const uint2 r4 = ld_in<CO>(quad_ptr(lr, q));
+    int p[4];
+    if (vec) {
+      const int4 p4 = ld_in<CO>(reinterpret_cast<const int4*>(parent + g0));
+      p[0] = p4.x;
+      p[1] = p4.y;
+      p[2] = p4.z;
+      p[3] = p4.w;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) p[j] = 4 * q + j < L.cn ? ld_in<CO>(parent + g0 + j) : g0 + j;
+    }
     const int v0 = lr * TC + 4 * q;
     const uint32_t e[4] = {r4.x & 0xffffu, r4.x >> 16, r4.y & 0xffffu, r4.y >> 16};
-    const int g0 = (L.r0 + lr) * Ws + L.c0 + 4 * q;  // scan index of the quad's first vertex
     int x[4];
     bool root[4];
 #pragma unroll
@@ -1140,20 +1157,20 @@ __device__ __forceinline__ void flatten_s1(const ScanDesc* d, const Loc& L, int3
       // entries past the tile's last column belong to the next tile or the
       // row padding
       root[j] = e[j] == (uint32_t)(v0 + j) && 4 * q + j < L.cn;
-      x[j] = g0 + j;
+      x[j] = root[j] ? p[j] : g0 + j;  // the first step of the chain, already loaded
     }
-    for (int it = 0; it < limit; ++it) {
-      bool more = false;
+    // the chains of the roots that a border join moved
+    bool walk[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) walk[j] = root[j] && x[j] != g0 + j;
+    for (int it = 0; it < limit && (walk[0] || walk[1] || walk[2] || walk[3]); ++it) {
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        if (!root[j]) continue;
-        const int p = ld_in<CO>(parent + x[j]);
-        if (p != x[j]) {
-          x[j] = p;
-          more = true;
-        }
+        if (!walk[j]) continue;
+        const int pp = ld_in<CO>(parent + x[j]);
+        if (pp != x[j]) x[j] = pp;
+        else walk[j] = false;
       }
-      if (!more) break;
     }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
