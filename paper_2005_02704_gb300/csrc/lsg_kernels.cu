@@ -157,10 +157,27 @@ __device__ __forceinline__ int find_done_sh(const int* P, int x, int limit) {
   return x;
 }
 
+// Joins the sets of a and b.  The two finds advance together, one
+// path-halving step of each per round, so that their shared-memory loads
+// are in flight at the same time.
 __device__ void union_sh(int* P, int a, int b, int limit, int32_t* err) {
+  volatile int* V = P;
   for (int it = 0; it < limit; ++it) {
-    a = find_sh(P, a, limit);
-    b = find_sh(P, b, limit);
+    int pa = V[a], pb = V[b];
+    for (int st = 0; (pa != a || pb != b) && st < limit; ++st) {
+      const int ga = pa != a ? V[pa] : a;
+      const int gb = pb != b ? V[pb] : b;
+      if (pa != a) {
+        if (ga != pa) V[a] = ga;
+        a = ga;
+      }
+      if (pb != b) {
+        if (gb != pb) V[b] = gb;
+        b = gb;
+      }
+      pa = V[a];
+      pb = V[b];
+    }
     if (a == b) return;
     if (a > b) {
       const int t = a;
