@@ -130,21 +130,10 @@ __device__ __forceinline__ const ScanDesc* tile_desc(const KArgs& a, int t, int&
 }
 
 // Union-find on shared memory.  P[x] <= x always holds, so the forest has no
-// cycles and the root of every tree is its smallest index.  find with path
-// halving: each visited node is re-pointed at its grandparent; the store
-// only shortens a path to an ancestor (P[x] <= x still holds), so it is safe
-// next to concurrent atomicMin links.
-__device__ __forceinline__ int find_sh(int* P, int x, int limit) {
-  volatile int* V = P;
-  int p = V[x];
-  while (p != x && limit-- > 0) {
-    const int gp = V[p];
-    if (gp != p) V[x] = gp;
-    x = gp;
-    p = V[x];
-  }
-  return x;
-}
+// cycles and the root of every tree is its smallest index.  Finds halve
+// paths: each visited node is re-pointed at its grandparent; the store only
+// shortens a path to an ancestor (P[x] <= x still holds), so it is safe next
+// to concurrent atomicMin links.
 
 // Root of x once every union is done (the forest no longer changes): plain
 // loads without path halving, so that independent chains overlap.
@@ -191,23 +180,27 @@ __device__ void union_sh(int* P, int a, int b, int limit, int32_t* err) {
   atomicOr(err, DERR_TIMEOUT);
 }
 
-// Union-find on global memory: loads bypass L1 (ld.global.cg) so they see the
-// atomics, which resolve in L2.  find with path halving, as above.
-__device__ __forceinline__ int find_halve(int32_t* P, int x, int limit) {
-  int p = __ldcg(P + x);
-  while (p != x && limit-- > 0) {
-    const int gp = __ldcg(P + p);
-    if (gp != p) __stcg(P + x, gp);
-    x = gp;
-    p = __ldcg(P + x);
-  }
-  return x;
-}
-
+// Joins the sets of a and b in the global union-find (same invariant, path
+// halving and interleaved finds as union_sh; loads bypass L1 with
+// ld.global.cg so they see the atomics, which resolve in L2): the two finds'
+// L2 round trips overlap.
 __device__ void union_g(int32_t* P, int a, int b, int limit, int32_t* err) {
   for (int it = 0; it < limit; ++it) {
-    a = find_halve(P, a, limit);
-    b = find_halve(P, b, limit);
+    int pa = __ldcg(P + a), pb = __ldcg(P + b);
+    for (int st = 0; (pa != a || pb != b) && st < limit; ++st) {
+      const int ga = pa != a ? __ldcg(P + pa) : a;
+      const int gb = pb != b ? __ldcg(P + pb) : b;
+      if (pa != a) {
+        if (ga != pa) __stcg(P + a, ga);
+        a = ga;
+      }
+      if (pb != b) {
+        if (gb != pb) __stcg(P + b, gb);
+        b = gb;
+      }
+      pa = __ldcg(P + a);
+      pb = __ldcg(P + b);
+    }
     if (a == b) return;
     if (a > b) {
       const int t = a;
