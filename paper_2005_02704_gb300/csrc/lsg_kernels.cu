@@ -135,15 +135,24 @@ __device__ __forceinline__ const ScanDesc* tile_desc(const KArgs& a, int t, int&
 // shortens a path to an ancestor (P[x] <= x still holds), so it is safe next
 // to concurrent atomicMin links.
 
-// Root of x once every union is done (the forest no longer changes): plain
-// loads without path halving, so that independent chains overlap.
-__device__ __forceinline__ int find_done_sh(const int* P, int x, int limit) {
-  int p = P[x];
-  while (p != x && limit-- > 0) {
-    x = p;
-    p = P[x];
+// Roots of a (when fa) and b (when fb) once every union is done (the forest
+// no longer changes): plain loads without path halving, the two chains
+// walked together so that their loads overlap; 0 for a chain not asked for.
+__device__ __forceinline__ void find_done2_sh(const int* P, bool fa, int a, bool fb, int b, int limit, int& ra,
+                                              int& rb) {
+  int pa = fa ? P[a] : a, pb = fb ? P[b] : b;
+  while ((pa != a || pb != b) && limit-- > 0) {
+    if (pa != a) {
+      a = pa;
+      pa = P[a];
+    }
+    if (pb != b) {
+      b = pb;
+      pb = P[b];
+    }
   }
-  return x;
+  ra = fa ? a : 0;
+  rb = fb ? b : 0;
 }
 
 // Joins the sets of a and b.  The two finds advance together, one
@@ -842,8 +851,7 @@ __device__ __forceinline__ void tile_cross_and_roots(const Loc& L, const uint8_t
     const int posA = (int)(ps & 0xffu), posB = (int)(ps >> 8);
     const int vA = lr * TC + lcA;
     int rA = 0, rB = 0;
-    if (act && posA == 2 * lane) rA = find_done_sh(lp, vA, G::NV + 1);
-    if (act && posB == 2 * lane + 1) rB = find_done_sh(lp, vA + 1, G::NV + 1);
+    find_done2_sh(lp, act && posA == 2 * lane, vA, act && posB == 2 * lane + 1, vA + 1, G::NV + 1, rA, rB);
     const uint32_t pub = (uint32_t)rA | ((uint32_t)rB << 16);
     const uint32_t gA = __shfl_sync(FULL, pub, posA >> 1), gB = __shfl_sync(FULL, pub, posB >> 1);
     if (act && lcA < L.cn) {
