@@ -297,11 +297,12 @@ def serve_measurement(args, local, world, max_over_ranks, sum_over_ranks):
     server = serve.Server(budget_bytes=8 << 30, lanes=3, max_batch=64, device=local)
     sat_n = min(len(trace), 4000)
     serve.run_served(server, feeds, trace[:sat_n], float("inf"))  # warm-up: slots for the deepest queue
+    k0 = len(server.batch_sizes)
     saturated = serve.run_served(server, feeds, trace[:sat_n], float("inf"))
+    k1 = len(server.batch_sizes)
     nominal = serve.run_served(server, feeds, trace, scale)
     pool_peak = server.pool.peak
-    nb = server.batches
-    mean_batch = float(sum(server.batch_sizes) / max(1, len(server.batch_sizes)))
+    sat_sizes, nom_sizes = server.batch_sizes[k0:k1], server.batch_sizes[k1:]
     server.close()
     serve.run_serial(feeds, trace[:50], float("inf"), device=local)  # warm-up
     serial = serve.run_serial(feeds, trace, scale, device=local)
@@ -310,7 +311,13 @@ def serve_measurement(args, local, world, max_over_ranks, sum_over_ranks):
     def agg(d):
         return {"p50_ms": max_over_ranks(d["p50_ms"]), "p99_ms": max_over_ranks(d["p99_ms"]),
                 "scans_per_s": sum_over_ranks(d["scans_per_s"]), "points_per_s": sum_over_ranks(d["points_per_s"]),
-                "scans": int(sum_over_ranks(d["scans"]))}
+                "scans": int(sum_over_ranks(d["scans"])),
+                # this rank's sensors (the shapes differ between ranks): no reduction
+                "p50_ms_by_shape": d["p50_ms_by_shape"]}
+
+    def batches(sizes):
+        return {"batches": len(sizes), "mean_batch": float(sum(sizes) / max(1, len(sizes))),
+                "share_of_one": float(sum(1 for x in sizes if x == 1) / max(1, len(sizes)))}
 
     return {"trace": f"8 sensors, 60 s simulated at {scale:g}x real time, {len(trace)} scans per GPU, "
                      "10-20 Hz Poisson + 4x burst [30,40) s, 8 GB admission budget, 3 lanes, batch <= 64",
@@ -318,7 +325,7 @@ def serve_measurement(args, local, world, max_over_ranks, sum_over_ranks):
             "saturated": {"batched": agg(saturated), "serial_plain": agg(serial_sat), "scans": sat_n},
             "p99_gain": serial["p99_ms"] / max(nominal["p99_ms"], 1e-9),
             "throughput_gain_saturated": saturated["scans_per_s"] / max(serial_sat["scans_per_s"], 1e-9),
-            "pool_peak_bytes": pool_peak, "batches": nb, "mean_batch": mean_batch}
+            "pool_peak_bytes": pool_peak, "batching": batches(nom_sizes), "batching_saturated": batches(sat_sizes)}
 
 
 def generator_measurement(specs, local, steps, warmup, max_over_ranks, sum_over_ranks):

@@ -449,9 +449,13 @@ def device_footprint(server: Server) -> int:
 def summarize(reqs: Sequence[Request], wall_s: float) -> dict:
     lat = np.array([(r.t_done - r.t_arrival) * 1e3 for r in reqs]) if reqs else np.zeros(1)
     pts = sum(r.key[0] * r.key[1] for r in reqs)
+    by_shape: Dict[str, List[float]] = {}
+    for r, x in zip(reqs, lat):
+        by_shape.setdefault(f"{r.key[0]}x{r.key[1]}" + (f"_s{r.key[2]}" if r.key[2] != 1 else ""), []).append(x)
     return {"scans": len(reqs), "points": pts, "wall_s": wall_s, "scans_per_s": len(reqs) / wall_s,
             "points_per_s": pts / wall_s, "p50_ms": float(np.percentile(lat, 50)),
-            "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat.max())}
+            "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat.max()),
+            "p50_ms_by_shape": {k: float(np.percentile(v, 50)) for k, v in sorted(by_shape.items())}}
 
 
 def make_feeds(specs, scans_per_sensor: int = 4, seed: int = 11) -> List[SensorFeed]:
