@@ -332,10 +332,12 @@ lsg_status lsg_plan_destroy(lsg_plan* plan);
  * Batched path from and to host memory (the problem of Sec. 2 end to end: a
  * scan with its ring elevations goes in, the mesh, normals and labels come
  * out).  Like lsg_batch_plan, plus the host transfers in the captured graph:
- * the batch is cut into `chunks` runs of consecutive scans with about equal
- * point counts; for each, the inputs io[b].xyzr and io[b].elevation are
- * copied into the device buffers scans[b] (x,y,z,r or ranges, by the scan's
- * form, and the elevations, all of which must be writable device memory),
+ * the batch is cut into `chunks` runs of consecutive scans whose point
+ * counts grow by a factor 1.1 from one run to the next (a small first run
+ * starts the copies back early); for each, the inputs io[b].xyzr and
+ * io[b].elevation are copied into the device buffers scans[b] (x,y,z,r or
+ * ranges, by the scan's form, and the elevations, all of which must be
+ * writable device memory),
  * the chunk's pass runs once they have landed, and the chunk's outputs are
  * copied into io[b].labels, .nseg, .meshbits and .normals (NULL ones
  * skipped) once its pass is done; the copies of neighbouring chunks, in both

@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <new>
 #include <vector>
 
@@ -685,14 +686,25 @@ cudaError_t issue(const std::vector<Copy>& v, cudaMemcpyKind kind, cudaStream_t 
   return cudaSuccess;
 }
 
-// Chunk boundaries: runs of consecutive scans with about equal point counts.
+// Chunk boundaries: runs of consecutive scans whose point counts grow by
+// kChunkGrowth from one chunk to the next.  The outputs cannot start back
+// before the first chunk's inputs have landed and its pass has run, so a
+// small first chunk starts the device -> host direction early; the growth
+// stays below the ratio at which a chunk's inputs would take longer to land
+// than the chunk before it takes to go back (the outputs are 17 bytes a
+// point against 16 in, and the link is slower that way), so the outputs
+// never wait once started.
+constexpr double kChunkGrowth = 1.1;
+
 std::vector<int> chunk_bounds(const lsg_plan* pl) {
   std::vector<int64_t> pts(pl->n + 1, 0);
   for (int b = 0; b < pl->n; ++b) pts[b + 1] = pts[b] + (int64_t)pl->dev_in[b].rings * pl->dev_in[b].cols;
   const int C = std::max(1, std::min(pl->chunks, pl->n));
+  std::vector<double> share(C + 1, 0.0);  // cumulative share of the points after c chunks
+  for (int c = 0; c < C; ++c) share[c + 1] = share[c] + std::pow(kChunkGrowth, c);
   std::vector<int> bounds{0};
   for (int c = 1; c < C; ++c) {
-    const int64_t target = pts[pl->n] * c / C;
+    const int64_t target = (int64_t)((double)pts[pl->n] * (share[c] / share[C]));
     int b = (int)(std::lower_bound(pts.begin(), pts.end(), target) - pts.begin());
     b = std::max(bounds.back() + 1, std::min(b, pl->n - (C - c)));
     bounds.push_back(b);
