@@ -341,10 +341,12 @@ lsg_status lsg_plan_destroy(lsg_plan* plan);
  * the chunk's pass runs once they have landed, and the chunk's outputs are
  * copied into io[b].labels, .nseg, .meshbits and .normals (NULL ones
  * skipped) once its pass is done; the copies of neighbouring chunks, in both
- * directions, run under each chunk's pass.  Consecutive scans whose host and
- * device buffers are contiguous share one copy.  lsg_batch_run replays the
- * whole sequence; the host outputs are complete once the stream has
- * synchronised, and the host inputs may be rewritten after that.
+ * directions, run under each chunk's pass.  The elevations of every scan go
+ * in ahead of the first chunk and the segment counts come back after the
+ * last.  Consecutive scans whose host and device buffers are contiguous
+ * share one copy.  lsg_batch_run replays the whole sequence; the host
+ * outputs are complete once the stream has synchronised, and the host inputs
+ * may be rewritten after that.
  *   io[n]      host buffers of every scan: page-locked memory (cudaHostAlloc
  *              or cudaHostRegister), else LSG_E_ARG; not copied, must
  *              outlive the plan.

@@ -726,7 +726,10 @@ static int plan_s1_only(const lsg_plan* pl, int b0, int b1) {
 // device on one branch, the chunk's pass (ring order, tiles, border joins,
 // labels) runs on a second once they have landed, and its outputs go device
 // -> host on a third once the pass is done, so that the copies of the
-// neighbouring chunks, in both directions, run under each chunk's pass.
+// neighbouring chunks, in both directions, run under each chunk's pass.  The
+// small copies (elevations in, segment counts out) go once for the whole
+// batch, ahead of the first chunk and after the last: every copy in the graph
+// costs a few microseconds of its own.
 static cudaError_t capture_io(lsg_plan* pl, cudaStream_t cs, int& launches) {
   cudaStream_t s_in = nullptr, s_run = nullptr, s_out = nullptr;
   std::vector<cudaEvent_t> evs;
@@ -746,9 +749,17 @@ static cudaError_t capture_io(lsg_plan* pl, cudaStream_t cs, int& launches) {
   const std::vector<int> bounds = chunk_bounds(pl);
   size_t h2d = 0, d2h = 0;
   launches = 0;
+  std::vector<Copy> elev_all, cnt_all;
+  for (int b = 0; b < pl->n; ++b) {
+    const ScanDesc& d = pl->host_desc[b];
+    if ((size_t)d.H * d.W)
+      add_copy(elev_all, const_cast<float*>(pl->dev_in[b].elevation), pl->io[b].elevation, sizeof(float) * d.H);
+    add_copy(cnt_all, pl->io[b].nseg, pl->dev_out[b].nseg, sizeof(int32_t));
+  }
+  if (e == cudaSuccess) e = issue(elev_all, cudaMemcpyHostToDevice, s_in, h2d);
   for (size_t c = 0; c + 1 < bounds.size() && e == cudaSuccess; ++c) {
     const int b0 = bounds[c], b1 = bounds[c + 1];
-    std::vector<Copy> in, elev, lab, cnt, mb, nrm;
+    std::vector<Copy> in, lab, mb, nrm;
     for (int b = b0; b < b1; ++b) {
       const lsg_scan& sc = pl->dev_in[b];
       const lsg_host_io& io = pl->io[b];
@@ -757,17 +768,14 @@ static cudaError_t capture_io(lsg_plan* pl, cudaStream_t cs, int& launches) {
       if (pts) {
         if (sc.xyzr) add_copy(in, const_cast<float*>(sc.xyzr), io.xyzr, pts * 16);
         else add_copy(in, const_cast<float*>(sc.range), io.xyzr, pts * 4);
-        add_copy(elev, const_cast<float*>(sc.elevation), io.elevation, sizeof(float) * d.H);
         add_copy(lab, io.labels, pl->dev_out[b].labels, pts * 4);
         add_copy(mb, io.meshbits, pl->dev_out[b].meshbits, nv);
         add_copy(nrm, io.normals, pl->dev_out[b].normals, nv * 12);
       }
-      add_copy(cnt, io.nseg, pl->dev_out[b].nseg, sizeof(int32_t));
     }
     cudaEvent_t ev_in = nullptr, ev_run = nullptr;
     if (e == cudaSuccess) e = new_event(&ev_in);
     if (e == cudaSuccess) e = new_event(&ev_run);
-    if (e == cudaSuccess) e = issue(elev, cudaMemcpyHostToDevice, s_in, h2d);
     if (e == cudaSuccess) e = issue(in, cudaMemcpyHostToDevice, s_in, h2d);
     if (e == cudaSuccess) e = cudaEventRecord(ev_in, s_in);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s_run, ev_in, 0);
@@ -794,11 +802,11 @@ static cudaError_t capture_io(lsg_plan* pl, cudaStream_t cs, int& launches) {
     }
     if (e == cudaSuccess) e = cudaEventRecord(ev_run, s_run);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s_out, ev_run, 0);
-    if (e == cudaSuccess) e = issue(cnt, cudaMemcpyDeviceToHost, s_out, d2h);
     if (e == cudaSuccess) e = issue(lab, cudaMemcpyDeviceToHost, s_out, d2h);
     if (e == cudaSuccess) e = issue(mb, cudaMemcpyDeviceToHost, s_out, d2h);
     if (e == cudaSuccess) e = issue(nrm, cudaMemcpyDeviceToHost, s_out, d2h);
   }
+  if (e == cudaSuccess) e = issue(cnt_all, cudaMemcpyDeviceToHost, s_out, d2h);
   for (cudaStream_t st : {s_in, s_run, s_out}) {
     cudaEvent_t join = nullptr;
     if (e == cudaSuccess) e = new_event(&join);
