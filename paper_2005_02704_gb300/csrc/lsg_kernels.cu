@@ -28,7 +28,9 @@
 //              seam with a lock-free atomicMin union-find over the roots.
 //   k_flatten  label = smallest full-resolution index of the component,
 //              back-fill of non-sampled points, segment count with warp
-//              reductions.                                [Algorithm 1; Sec. 2 end]
+//              reductions (k_flatten1: the same for launches whose scans all
+//              have s = 1, where every point is a vertex).
+//                                                         [Algorithm 1; Sec. 2 end]
 //
 // Labels are exact: every union hooks the larger root under the smaller, so
 // each component's root is its smallest vertex index whatever the thread
@@ -1431,6 +1433,26 @@ __global__ void __launch_bounds__(NT_FLAT, (flat_min_blocks<TR, NW>())) k_flatte
   }
 }
 
+// Labels of a launch whose scans all have s = 1: the register-resident pass
+// alone, compiled without the general back-fill path, whose state made the
+// shared kernel spill more at the same register budget.  A scan with s > 1
+// is refused through the error word (its labels stay unwritten).
+template <int TR, int NW>
+__global__ void __launch_bounds__(NT_FLAT, (flat_min_blocks<TR, NW>())) k_flatten1(const __grid_constant__ KArgs a) {
+  extern __shared__ __align__(16) unsigned char fsm[];
+  dep_wait();
+  for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+    int lt;
+    const ScanDesc* d = tile_desc(a, t, lt);
+    const Loc L = make_loc(d, lt, TR, NW * SO);
+    if (L.s == 1)
+      flatten_s1<TR, NW, NT_FLAT, false>(d, L, reinterpret_cast<int32_t*>(fsm + FlatGeo<TR, NW>::off_lab));
+    else if (threadIdx.x == 0)
+      atomicOr(a.err, DERR_LAUNCH);
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------------------------------------
 // k_fused: the whole batched pass in one persistent launch
 // ---------------------------------------------------------------------------
@@ -1518,6 +1540,9 @@ static cudaError_t set_attrs() {
   e = cudaFuncSetAttribute(k_flatten<TR, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)FlatGeo<TR, NW>::bytes);
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_flatten1<TR, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)FlatGeo<TR, NW>::s1_bytes);
+  if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_fused<TR, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)FusedGeo<TR, NW>::bytes);
   if (e != cudaSuccess) return e;
@@ -1592,8 +1617,8 @@ static cudaError_t run_merge(const KArgs& a, cudaStream_t st, bool pdl) {
 }
 template <int TR, int NW>
 static cudaError_t run_flatten(const KArgs& a, cudaStream_t st, bool pdl) {
-  return launch_k(k_flatten<TR, NW>, a.ntiles, NT_FLAT,
-                  a.s1_only ? FlatGeo<TR, NW>::s1_bytes : FlatGeo<TR, NW>::bytes, st, pdl, a);
+  if (a.s1_only) return launch_k(k_flatten1<TR, NW>, a.ntiles, NT_FLAT, FlatGeo<TR, NW>::s1_bytes, st, pdl, a);
+  return launch_k(k_flatten<TR, NW>, a.ntiles, NT_FLAT, FlatGeo<TR, NW>::bytes, st, pdl, a);
 }
 
 template <int TR, int NW>
