@@ -167,7 +167,8 @@ enum {
   LSG_TILE_16x120 = 5,
   LSG_TILE_8x120 = 6,
   LSG_TILE_4x120 = 7,
-  LSG_TILE_COUNT = 8
+  LSG_TILE_2x120 = 8,
+  LSG_TILE_COUNT = 9
 };
 
 /* Fills *p with the defaults listed above. */
@@ -187,10 +188,10 @@ lsg_status lsg_destroy(lsg_ctx* ctx);
 /* Selects the tile shape of the context's calls (lsg_segment,
  * lsg_label_from_mask, lsg_batch_launch, lsg_spin_begin, and lsg_batch_plan
  * given LSG_TILE_AUTO).  LSG_TILE_AUTO (the default) lets each call pick from
- * its work: the first of 32x120, 32x240, 16x240, 16x120, 8x120, 4x120 that
- * gives at least four tiles per SM, else the one that gives the most tiles
- * (small scans fill the GPU with small tiles of short row sweeps, large
- * batches keep the efficient ones). */
+ * its work: the first of 32x120, 32x240, 16x240, 16x120, 8x120, 4x120,
+ * 2x120 that gives at least four tiles per SM, else the one that gives the
+ * most tiles (small scans fill the GPU with small tiles of short row sweeps,
+ * large batches keep the efficient ones). */
 lsg_status lsg_set_tile(lsg_ctx* ctx, int tile);
 
 /*

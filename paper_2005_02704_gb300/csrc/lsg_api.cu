@@ -958,10 +958,10 @@ static lsg_status plan_create(lsg_ctx* ctx, int32_t n, const lsg_scan* scans, co
     Hs[b] = scans[b].cols > 0 ? scans[b].rings : 0;
   }
   if (tile == LSG_TILE_AUTO) tile = pick_tile(Hs.data(), Ws.data(), n, ctx->sms);
-  // bound on the tile table over every tile shape (at least 4 rows x 120 columns)
+  // bound on the tile table over every tile shape (at least 2 rows x 120 columns)
   size_t tiles_max = 0;
   for (int b = 0; b < n; ++b)
-    tiles_max += (size_t)(scans[b].rings / 4 + 1) * (Ws[b] / 120 + 1);
+    tiles_max += (size_t)(scans[b].rings / 2 + 1) * (Ws[b] / 120 + 1);
   // workspace, descriptors, tile table, fused schedule (scan + 3 items per tile) and counters
   const size_t bytes = ws_total + align_up(sizeof(ScanDesc) * n, 256) + sizeof(int32_t) * tiles_max +
                        sizeof(int2) * (n + 3 * tiles_max) + sizeof(int32_t) * (1 + 3 * (size_t)n);

@@ -68,17 +68,18 @@ TileShape tile_shape(int tile) {
     case LSG_TILE_16x120: return {16, 120};
     case LSG_TILE_8x120: return {8, 120};
     case LSG_TILE_4x120: return {4, 120};
+    case LSG_TILE_2x120: return {2, 120};
     case LSG_TILE_16x240:
     default: return {16, 240};
   }
 }
 
 int pick_tile(const int* H, const int* Ws, int n, int sms) {
-  static const int order[6] = {LSG_TILE_32x120, LSG_TILE_32x240, LSG_TILE_16x240, LSG_TILE_16x120,
-                               LSG_TILE_8x120,  LSG_TILE_4x120};
+  static const int order[7] = {LSG_TILE_32x120, LSG_TILE_32x240, LSG_TILE_16x240, LSG_TILE_16x120,
+                               LSG_TILE_8x120,  LSG_TILE_4x120,  LSG_TILE_2x120};
   int best = order[0];
   long long best_n = -1;
-  for (int k = 0; k < 6; ++k) {
+  for (int k = 0; k < 7; ++k) {
     const TileShape ts = tile_shape(order[k]);
     long long nt = 0;
     for (int b = 0; b < n; ++b)
@@ -1560,6 +1561,7 @@ cudaError_t prepare_kernels() {
   if ((e = set_attrs<16, 2>()) != cudaSuccess) return e;
   if ((e = set_attrs<8, 2>()) != cudaSuccess) return e;
   if ((e = set_attrs<4, 2>()) != cudaSuccess) return e;
+  if ((e = set_attrs<2, 2>()) != cudaSuccess) return e;
   return cudaSuccess;
 }
 
@@ -1600,6 +1602,7 @@ cudaError_t launch_prep(const KArgs& a, cudaStream_t st) {
     case LSG_TILE_16x120: return FN<16, 2>(__VA_ARGS__);  \
     case LSG_TILE_8x120: return FN<8, 2>(__VA_ARGS__);    \
     case LSG_TILE_4x120: return FN<4, 2>(__VA_ARGS__);    \
+    case LSG_TILE_2x120: return FN<2, 2>(__VA_ARGS__);    \
     default: return FN<16, 4>(__VA_ARGS__);               \
   }
 

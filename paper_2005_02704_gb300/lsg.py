@@ -20,7 +20,8 @@ from . import _build
 LSG_OK, LSG_E_ARG, LSG_E_SHAPE, LSG_E_OOM, LSG_E_BUDGET, LSG_E_CUDA, LSG_E_TIMEOUT, LSG_E_DEVICE = range(8)
 LSG_PRED_ANGLE, LSG_PRED_COMPONENT = 0, 1
 LSG_TILE_AUTO = -1
-TILES = {"16x240": 0, "32x120": 1, "32x240": 2, "32x480": 3, "64x240": 4, "16x120": 5, "8x120": 6, "4x120": 7}
+TILES = {"16x240": 0, "32x120": 1, "32x240": 2, "32x480": 3, "64x240": 4, "16x120": 5, "8x120": 6, "4x120": 7,
+         "2x120": 8}
 LSG_TILE_COUNT = len(TILES)
 
 BIT_R, BIT_D, BIT_G = 0x01, 0x02, 0x04

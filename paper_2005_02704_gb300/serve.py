@@ -166,7 +166,7 @@ class Server:
         # charged to the budget first, and the slots share the rest
         H, W, s_ = max_shape
         Ws = lsg.ws_of(W, s_)
-        tiles = ((H + 3) // 4 + 1) * (Ws // 120 + 1)  # the smallest tile shape: 4 x 120
+        tiles = ((H + 1) // 2 + 1) * (Ws // 120 + 1)  # the smallest tile shape: 2 x 120
         self.ctxs = [lsg.Context(device, budget_bytes=budget_bytes) for _ in range(lanes)]
         for c in self.ctxs:
             lsg.lsg_reserve(c.h, max_batch * lsg.scan_workspace_bytes(H, Ws), max_batch, 2 * max_batch * tiles)

@@ -56,7 +56,8 @@ def mixed_specs(n, seed0):
 
 
 @pytest.mark.parametrize("schedule", [1, 0, 2], ids=["fused", "phased", "grouped"])
-@pytest.mark.parametrize("tile", ["16x240", "32x120", "32x240", "32x480", "64x240", "16x120", "8x120", "4x120"])
+@pytest.mark.parametrize("tile", ["16x240", "32x120", "32x240", "32x480", "64x240", "16x120", "8x120", "4x120",
+                                  "2x120"])
 def test_batch_equals_per_scan(ctx, tile, schedule):
     lsg, _ = mods()
     specs = mixed_specs(12, 5000)

@@ -87,7 +87,7 @@ def test_auto_tile_equals_fixed(ctx, make):
     lsg.lsg_set_tile(ctx.h, lsg.LSG_TILE_AUTO)
     auto = run_gpu(ctx, scan, p)
     lsg.lsg_set_tile(ctx.h, lsg.LSG_TILE_AUTO)
-    for tile in ("32x240", "16x120", "8x120", "4x120"):
+    for tile in ("32x240", "16x120", "8x120", "4x120", "2x120"):
         fixed = run_gpu(ctx, scan, p, tile=lsg.TILES[tile])
         for a, b in zip(auto, fixed):
             assert np.array_equal(a, b), tile
@@ -120,6 +120,7 @@ RAGGED = [
     (35, 121, 1, 0, "32x120"), (17, 121, 1, 1, "16x120"), (33, 361, 2, 1, "16x120"), (16, 120, 1, 0, "16x120"),
     (9, 241, 1, 1, "8x120"), (8, 120, 3, 0, "8x120"), (25, 1800, 1, 1, "8x120"),
     (3, 130, 1, 1, "4x120"), (13, 483, 2, 0, "4x120"), (16, 1800, 1, 1, "4x120"),
+    (3, 130, 1, 1, "2x120"), (13, 483, 2, 0, "2x120"), (7, 241, 1, 1, "2x120"), (16, 1800, 1, 1, "2x120"),
 ]
 
 
@@ -133,7 +134,7 @@ def test_ragged_shapes(ctx, H, W, s, wrap, tile):
 
 
 RANGE_RAGGED = [(17, 257, 3, 0, "4x120"), (9, 131, 1, 1, "8x120"), (33, 361, 2, 1, "16x120"),
-                (5, 1030, 1, 1, "32x240"), (35, 121, 1, 0, "32x120")]
+                (5, 1030, 1, 1, "32x240"), (35, 121, 1, 0, "32x120"), (5, 361, 3, 1, "2x120")]
 
 
 @pytest.mark.parametrize("H,W,s,wrap,tile", RANGE_RAGGED)
@@ -214,7 +215,7 @@ def test_label_from_mask_random_masks(ctx):
             flat[hom] |= hb
         mb = flat.reshape(H, Ws)
         want, nwant = O.label_from_mask(mb, valid_full, W, s, wrap)
-        for tile in ("16x240", "32x120", "32x480", "16x120", "8x120", "4x120"):
+        for tile in ("16x240", "32x120", "32x480", "16x120", "8x120", "4x120", "2x120"):
             lsg.lsg_set_tile(ctx.h, lsg.TILES[tile])
             got, n = ctx.label_from_mask(torch.from_numpy(mb).to(dev), torch.from_numpy(valid_full).to(dev), W, s,
                                          wrap)

@@ -53,7 +53,7 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("tile", ["32x120", "16x240", "32x480", "16x120", "8x120", "4x120"])
+@pytest.mark.parametrize("tile", ["32x120", "16x240", "32x480", "16x120", "8x120", "4x120", "2x120"])
 @pytest.mark.parametrize("name,spec,wrap,npush", CASES, ids=[c[0] for c in CASES])
 def test_spin_equals_segment(ctx, name, spec, wrap, npush, tile):
     lsg = mod()
