@@ -321,7 +321,7 @@ def serve_measurement(args, local, world, max_over_ranks, sum_over_ranks):
 
     return {"trace": f"8 sensors, 60 s simulated at {scale:g}x real time, {len(trace)} scans per GPU, "
                      "10-20 Hz Poisson + 4x burst [30,40) s, 8 GB admission budget, 3 lanes, batch <= 64",
-            "batched": agg(nominal), "serial_plain": agg(serial),
+            "batched": agg(nominal), "serial_plain": agg(serial)
             "saturated": {"batched": agg(saturated), "serial_plain": agg(serial_sat), "scans": sat_n},
             "p99_gain": serial["p99_ms"] / max(nominal["p99_ms"], 1e-9),
             "throughput_gain_saturated": saturated["scans_per_s"] / max(serial_sat["scans_per_s"], 1e-9),
@@ -420,9 +420,12 @@ def single_scan_measurement(local, peak, reps=100, warm=10):
                      "points_per_s": n / (p50 / 1e3), "scans_per_s": 1e3 / p50, "bytes_per_point": bpp,
                      "achieved_gbs": bpp * n / (p50 / 1e3) / 1e9,
                      "hbm_frac": bpp * n / (p50 / 1e3) / 1e9 / peak}
+        res[name]["host_io"] = host_io_latency(ctx, scan, p, local, reps, warm)
     ctx.close()
     res["note"] = (f"{reps} back-to-back lsg_segment calls per scan after {warm} warm-up calls, tile shape per call; "
-                   "L2-resident (latency-bound, not HBM-bound)")
+                   "L2-resident (latency-bound, not HBM-bound); host_io: lsg_batch_launch_io of the scan alone from "
+                   "and to pinned host memory (x,y,z,r and elevations in; labels, count, mesh bytes and normals out), "
+                   "events around each call, one call at a time")
     # the L2 side of the largest single scan, from the committed one-kernel
     # ncu capture of its tile kernel (null once the kernels have changed)
     vals = profiled_values("single_scan_k_tile.md")
@@ -435,6 +438,57 @@ def single_scan_measurement(local, peak, reps=100, warm=10):
         except (KeyError, ValueError):
             pass
     return res
+
+
+def host_io_latency(ctx, scan, p, local, reps, warm):
+    """End-to-end device time of one scan from and to pinned host memory:
+    lsg_batch_launch_io with n = 1 (x,y,z,r and elevations in; labels, count,
+    mesh bytes and normals out), events around each call, one call at a time
+    as a request waits for its results; p50 / p99 of `reps` calls."""
+    import torch
+
+    from paper_2005_02704_gb300 import lsg
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    H, W, s_ = scan.rings, scan.cols, p.subsample
+    Ws = lsg.ws_of(W, s_)
+    hx = torch.empty(scan.xyzr.shape, dtype=torch.float32, pin_memory=True)
+    hx.numpy()[...] = scan.xyzr
+    he = torch.empty(H, dtype=torch.float32, pin_memory=True)
+    he.numpy()[...] = scan.elev
+    hl = torch.empty((H, W), dtype=torch.int32, pin_memory=True)
+    hn = torch.empty(1, dtype=torch.int32, pin_memory=True)
+    hm = torch.empty((H, Ws), dtype=torch.uint8, pin_memory=True)
+    hv = torch.empty((H, Ws, 3), dtype=torch.float32, pin_memory=True)
+    x = torch.empty((H, W, 4), dtype=torch.float32, device=dev)
+    e = torch.empty(H, dtype=torch.float32, device=dev)
+    out = lsg.alloc_outputs(H, W, s_, dev)
+    io = (lsg.lsg_host_io * 1)()
+    io[0].xyzr, io[0].elevation, io[0].labels = hx.data_ptr(), he.data_ptr(), hl.data_ptr()
+    io[0].nseg, io[0].meshbits, io[0].normals = hn.data_ptr(), hm.data_ptr(), hv.data_ptr()
+    sa = (lsg.lsg_scan * 1)(lsg.make_scan(e, xyzr=x, az0=scan.az0, daz=scan.daz))
+    pa = (lsg.lsg_params * 1)(p.to_c())
+    oa = (lsg.lsg_out * 1)(out.to_c())
+
+    def call():
+        rc = lsg.lsg_batch_launch_io(ctx.h, sa, pa, oa, io, stream.cuda_stream)
+        if rc != lsg.LSG_OK:
+            raise lsg.LsgError(rc, "lsg_batch_launch_io")
+
+    for _ in range(warm):
+        call()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    torch.cuda.synchronize()
+    for a, b in ev:
+        a.record(stream)
+        call()
+        b.record(stream)
+        b.synchronize()
+    if ctx.error() != lsg.LSG_OK:
+        raise RuntimeError("device error in the host-buffer single-scan measurement")
+    t = sorted(a.elapsed_time(b) for a, b in ev)
+    return {"bytes_in": H * W * 16 + H * 4, "bytes_out": H * W * 4 + 4 + H * Ws * 13,
+            "p50_ms": pct(t, 0.5), "p99_ms": pct(t, 0.99)}
 
 
 def oracle_single_scans(reps=3):

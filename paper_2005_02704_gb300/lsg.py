@@ -219,8 +219,14 @@ def lsg_batch_launch(ctx: int, scans, params, outs, stream: int = 0) -> int:
 
 def lsg_batch_launch_io(ctx: int, scans, params, outs, io, stream: int = 0) -> int:
     """lsg_batch_launch plus the host->device input and device->host result
-    copies of each scan (ctypes arrays).  Returns the status code."""
-    return load().lsg_batch_launch_io(ctx, len(scans), scans, params, outs, io, stream or None)
+    copies of each scan (sequences or ctypes arrays of lsg_scan / lsg_params /
+    lsg_out / lsg_host_io).  Returns the status code."""
+    n = len(scans)
+    sa = scans if isinstance(scans, ctypes.Array) else (lsg_scan * n)(*scans)
+    pa = params if isinstance(params, ctypes.Array) else (lsg_params * n)(*params)
+    oa = outs if isinstance(outs, ctypes.Array) else (lsg_out * n)(*outs)
+    ia = io if isinstance(io, ctypes.Array) else (lsg_host_io * n)(*io)
+    return load().lsg_batch_launch_io(ctx, n, sa, pa, oa, ia, stream or None)
 
 
 def lsg_reserve(ctx: int, workspace_bytes: int, max_scans: int, max_tiles: int) -> None:
