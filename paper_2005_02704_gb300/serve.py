@@ -120,6 +120,8 @@ class Request:
     keep_geometry: bool = False
     result: Optional[dict] = None
     c_params: object = None        # cached lsg_params of the sensor
+    ref_params: object = None      # and a ctypes reference to it
+    host_ptrs: object = None       # (x,y,z,r, elevations) host addresses
 
 
 class Slot:
@@ -142,6 +144,9 @@ class Slot:
         self.c_io = lsg.lsg_host_io()
         self.c_io.labels = self.h_labels.data_ptr() if self.h_labels.numel() else None
         self.c_io.nseg = self.h_nseg.data_ptr()
+        # references for the batch-of-one call, made once
+        self.ref_scan, self.ref_out, self.ref_io = (ctypes.byref(self.c_scan), ctypes.byref(self.c_out),
+                                                    ctypes.byref(self.c_io))
 
     def geometry_buffers(self):
         import torch
@@ -178,6 +183,11 @@ class Server:
         self.max_shape = max_shape
         self.shapes_ok = set()
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(lanes)]
+        # what the batch-of-one launch passes, looked up once: the entry
+        # point, the contexts' and streams' handles
+        self._launch_io = lsg.load().lsg_batch_launch_io
+        self._ctx_h = [c.h for c in self.ctxs]
+        self._stream_h = [int(st.cuda_stream) for st in self.streams]
         self.events = [torch.cuda.Event() for _ in range(lanes)]
         self.inflight: List[Optional[List[Request]]] = [None] * lanes
         self.n_inflight = 0
@@ -240,6 +250,9 @@ class Server:
         n = len(batch)
         if n == 1:
             # a batch of one passes the slot's own descriptors by reference
+            # (references, handles and host addresses prepared beforehand: the
+            # input copy is the call's first step, so every step before the
+            # call delays the scan)
             req = batch[0]
             slot = req.slot
             req.t_launch = now
@@ -247,8 +260,11 @@ class Server:
             sc.azimuth0 = req.az0
             sc.azimuth_step = req.daz
             h = slot.c_io
-            h.xyzr = req.host_xyzr.data_ptr()
-            h.elevation = req.host_elev.data_ptr()
+            if req.host_ptrs is not None:
+                h.xyzr, h.elevation = req.host_ptrs
+            else:
+                h.xyzr = req.host_xyzr.data_ptr()
+                h.elevation = req.host_elev.data_ptr()
             if req.keep_geometry:
                 mbh, nrh = slot.geometry_buffers()
                 h.meshbits = mbh.data_ptr() if mbh.numel() else None
@@ -256,9 +272,11 @@ class Server:
             else:
                 h.meshbits = None
                 h.normals = None
-            prm = req.c_params if req.c_params is not None else req.params.to_c()
-            rc = lsg.load().lsg_batch_launch_io(self.ctxs[k].h, 1, ctypes.byref(sc), ctypes.byref(prm),
-                                                ctypes.byref(slot.c_out), ctypes.byref(h), int(st.cuda_stream))
+            prm = req.ref_params
+            if prm is None:
+                prm = ctypes.byref(req.c_params if req.c_params is not None else req.params.to_c())
+            rc = self._launch_io(self._ctx_h[k], 1, slot.ref_scan, prm, slot.ref_out, slot.ref_io,
+                                 self._stream_h[k])
             if rc != lsg.LSG_OK:
                 raise lsg.LsgError(rc, "lsg_batch_launch_io")
             self.events[k].record(st)
@@ -332,6 +350,8 @@ class SensorFeed:
     daz: float
     params: "lsg.Params"
     c_params: object = None
+    ref_params: object = None
+    host_ptrs: object = None       # (x,y,z,r, elevations) host address per scan
 
 
 def arrival_trace(rates: Sequence[float], duration_s: float = 60.0, burst=(30.0, 40.0, 4.0),
@@ -351,11 +371,15 @@ def arrival_trace(rates: Sequence[float], duration_s: float = 60.0, burst=(30.0,
 
 
 def _request(feed: SensorFeed, ticket: int, t_arrival: float, keep_geometry: bool = False) -> Request:
-    x = feed.host_xyzr[ticket % len(feed.host_xyzr)]
+    m = ticket % len(feed.host_xyzr)
     if feed.c_params is None:
         feed.c_params = feed.params.to_c()
-    return Request(ticket, feed.sensor, feed.key, x, feed.host_elev, feed.az0, feed.daz, feed.params, t_arrival,
-                   keep_geometry=keep_geometry, c_params=feed.c_params)
+        feed.ref_params = ctypes.byref(feed.c_params)
+        e = feed.host_elev.data_ptr()
+        feed.host_ptrs = [(x.data_ptr(), e) for x in feed.host_xyzr]
+    return Request(ticket, feed.sensor, feed.key, feed.host_xyzr[m], feed.host_elev, feed.az0, feed.daz,
+                   feed.params, t_arrival, keep_geometry=keep_geometry, c_params=feed.c_params,
+                   ref_params=feed.ref_params, host_ptrs=feed.host_ptrs[m])
 
 
 @contextlib.contextmanager
@@ -386,12 +410,13 @@ def run_served(server: Server, feeds: Sequence[SensorFeed], trace, time_scale: f
 
 def _run_served(server: Server, feeds: Sequence[SensorFeed], trace, time_scale: float,
                 keep_geometry: bool) -> dict:
-    t0 = time.perf_counter()
-    i = 0
+    clock = time.perf_counter
+    t0 = clock()
+    i, n = 0, len(trace)
     reqs = []
-    while i < len(trace) or server.busy():
-        now = time.perf_counter()
-        while i < len(trace) and trace[i][0] / time_scale <= now - t0:
+    while i < n or server.pending or server.n_inflight:
+        now = clock()
+        while i < n and trace[i][0] / time_scale <= now - t0:
             tv, k = trace[i]
             r = _request(feeds[k], i, t0 + tv / time_scale, keep_geometry)
             reqs.append(r)
