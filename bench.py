@@ -321,7 +321,7 @@ def serve_measurement(args, local, world, max_over_ranks, sum_over_ranks):
 
     return {"trace": f"8 sensors, 60 s simulated at {scale:g}x real time, {len(trace)} scans per GPU, "
                      "10-20 Hz Poisson + 4x burst [30,40) s, 8 GB admission budget, 3 lanes, batch <= 64",
-            "batched": agg(nominal), "serial_plain": agg(serial)
+            "batched": agg(nominal), "serial_plain": agg(serial),
             "saturated": {"batched": agg(saturated), "serial_plain": agg(serial_sat), "scans": sat_n},
             "p99_gain": serial["p99_ms"] / max(nominal["p99_ms"], 1e-9),
             "throughput_gain_saturated": saturated["scans_per_s"] / max(serial_sat["scans_per_s"], 1e-9),

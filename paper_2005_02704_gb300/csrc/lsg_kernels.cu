@@ -499,6 +499,10 @@ __device__ __forceinline__ void tile_sweep(const ScanDesc* __restrict__ d, const
   const bool outB = strip && lcA + 1 < L.cn;        // second column is an output
   const int nsteps = L.rn + 3;  // rows r0-1 .. r0+rn+1
   unsigned vout = (unsigned)L.r0 * (unsigned)L.Ws + (unsigned)(L.c0 + lcA);  // output vertex, tile row 0
+  // the output arrays' bases in registers (read through d every row, they
+  // would be reloaded after each store, which might alias the descriptor)
+  uint8_t* const mb_out = d->mb;
+  float* const nrm_out = d->nrm;
 
   auto fetch = [&](int q, int k) {
     const long long ro = rows_s[k];
@@ -635,8 +639,8 @@ __device__ __forceinline__ void tile_sweep(const ScanDesc* __restrict__ d, const
           const bool hasA = m2A & B_HASN, hasB = m2B & B_HASN;
           const float oxA = hasA ? nx2.x : 0.f, oyA = hasA ? ny2.x : 0.f, ozA = hasA ? nz2.x : 0.f;
           const float oxB = hasB ? nx2.y : 0.f, oyB = hasB ? ny2.y : 0.f, ozB = hasB ? nz2.y : 0.f;
-          uint8_t* mp = d->mb + vout;
-          float* np = d->nrm + 3 * (size_t)vout;
+          uint8_t* mp = mb_out + vout;
+          float* np = nrm_out + 3 * (size_t)vout;
           if (outB && ((reinterpret_cast<uintptr_t>(mp) & 1) == 0)) {
             *reinterpret_cast<uint16_t*>(mp) = (uint16_t)(bA | (bB << 8));
           } else {
