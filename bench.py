@@ -832,7 +832,10 @@ def main():
         plain = {"value": pts_all / (ms_plain / 1e3), "unit": UNIT, "ms_per_pass": ms_plain,
                  "host_enqueue_ms_per_pass": host_ms,
                  "scans_per_s": db.n * world / (ms_plain / 1e3),
-                 "gpu_launches_per_pass": 4 * db.n, "tile": "auto (per call)"}
+                 # a single-scan call of at most 256 rings launches three kernels (its
+                 # tile kernel finds the ring order), a larger one four
+                 "gpu_launches_per_pass": sum(3 if sh.rings <= 256 else 4 for sh in db.shapes),
+                 "tile": "auto (per call)"}
 
     # ---- served path: continuous batching of 8 sensors vs a serial loop ---
     served = None

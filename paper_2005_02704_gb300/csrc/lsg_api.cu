@@ -211,9 +211,16 @@ int ctx_tile(const lsg_ctx* ctx, const int* H, const int* Ws, int n) {
 
 lsg_status run_pass(KArgs a, int tile, bool geometry, cudaStream_t st) {
   a.s1_only = a.one.s == 1;
-  // the three kernels after k_prep start while their predecessor drains
-  cudaError_t e = launch_prep(a, st);
-  if (e == cudaSuccess) e = geometry ? launch_tile(tile, a, st, true) : launch_tile_ccl(tile, a, st, true);
+  cudaError_t e = cudaSuccess;
+  if (geometry && a.one.H <= kFuseMaxRings) {
+    // no k_prep: each tile finds the ring order of the rows it reads
+    a.fuse_prep = 1;
+    e = launch_tile(tile, a, st, false);
+  } else {
+    // the kernels after k_prep start while their predecessor drains
+    e = launch_prep(a, st);
+    if (e == cudaSuccess) e = geometry ? launch_tile(tile, a, st, true) : launch_tile_ccl(tile, a, st, true);
+  }
   if (e == cudaSuccess) e = launch_merge(tile, a, st, true);
   if (e == cudaSuccess) e = launch_flatten(tile, a, st, true);
   return cuda_status(e);

@@ -47,8 +47,15 @@ struct KArgs {
   int32_t* err;              // device error word
   int32_t s1_only;           // 1: every scan of the launch has s = 1 (the label
                              // kernel then needs less shared memory)
+  int32_t fuse_prep;         // 1: single scan, no k_prep before the tile kernel:
+                             // each tile finds the ring order of the rows it reads
+                             // (at most kFuseMaxRings rings)
   ScanDesc one;
 };
+
+// Rings of a single scan up to which the tile kernel finds the ring order
+// itself (its elevations fit in the tile's idle row slots).
+constexpr int kFuseMaxRings = 256;
 
 // The persistent fused pass: one launch that walks a schedule of work items
 // (ring order of a scan, then its tiles, border merges and labels), each item

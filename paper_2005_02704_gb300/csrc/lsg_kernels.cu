@@ -875,9 +875,76 @@ __device__ __forceinline__ void tile_cross_and_roots(const Loc& L, const uint8_t
   }
 }
 
+// The row table of tile_body for a single scan launched without k_prep
+// (KArgs::fuse_prep, H <= kFuseMaxRings): the tile finds the input rows of
+// the sorted rings it reads (r0-1 .. r0+rn+1; elevations descending, ties by
+// input row, as k_prep's rank count orders them).  Elevations that fall
+// strictly along the input rows give the identity order, strictly rising
+// ones its reverse; otherwise every ring's rank is counted, and a NaN
+// elevation is flagged.  Tiles of the first tile column also store the ring
+// order of their own rows (read by the back-fill at s > 1), and tile 0
+// clears the segment count.  The elevations sit in the sweep's row slots,
+// idle until the sweep starts.
+template <int TR, int NW>
+__device__ __forceinline__ void tile_rows_fused(const ScanDesc* d, const Loc& L, int lt, unsigned char* smem,
+                                                int32_t* err) {
+  using G = Geo<TR, NW>;
+  static_assert(G::ring_bytes >= sizeof(float) * kFuseMaxRings, "elevations fit in the row slots");
+  long long* rows_s = reinterpret_cast<long long*>(smem + G::off_rows);
+  float2* trig_s = reinterpret_cast<float2*>(smem + G::off_trig);
+  float* se = reinterpret_cast<float*>(smem + G::off_ring);
+  const int H = L.H, nk = L.rn + 3;
+  bool desc = true, asc = true;
+  for (int k = threadIdx.x; k < H; k += G::NT) {
+    const float e = __ldg(d->elev + k);
+    se[k] = e;
+    if (k + 1 < H) {
+      const float f = __ldg(d->elev + k + 1);
+      desc = desc && e > f;
+      asc = asc && e < f;
+    }
+  }
+  for (int k = threadIdx.x; k < nk + RING - 1; k += G::NT) {
+    rows_s[k] = -1;  // absent unless a ring of the scan lands there
+    if (k < nk) trig_s[k] = make_float2(0.f, 1.f);
+  }
+  desc = __syncthreads_and(desc);
+  asc = __syncthreads_and(asc);
+  auto place = [&](int q, int i) {  // input row q is sorted ring i
+    const int k = i - (L.r0 - 1);
+    if (k < 0 || k >= nk) return;
+    rows_s[k] = (long long)q * L.W;
+    if (!d->xyzr) {
+      float sn, cs;
+      sincosf(se[q], &sn, &cs);
+      trig_s[k] = make_float2(sn, cs);
+    }
+    if (L.c0 == 0 && k >= 1 && k <= L.rn) d->order[i] = q;
+  };
+  if (desc || asc) {
+    for (int k = threadIdx.x; k < nk; k += G::NT) {
+      const int i = L.r0 - 1 + k;
+      if (i >= 0 && i < H) place(desc ? i : H - 1 - i, i);
+    }
+  } else {
+    for (int q = threadIdx.x; q < H; q += G::NT) {
+      const float e = se[q];
+      if (e != e) atomicOr(err, DERR_NAN_ELEV);
+      int rank = 0;
+      for (int m = 0; m < H; ++m) {
+        const float em = se[m];
+        rank += (em > e) || (em == e && m < q);
+      }
+      if (rank < H) place(q, rank);
+    }
+  }
+  if (lt == 0 && threadIdx.x == 0) *d->nseg = 0;
+}
+
 // One tile of one scan: decode + mesh + normals + edge mask + tile
-// components (smem: Geo<TR,NW>::bytes of dynamic shared memory).
-template <int TR, int NW, bool CO = false>
+// components (smem: Geo<TR,NW>::bytes of dynamic shared memory).  FUSE: the
+// ring order comes from tile_rows_fused instead of k_prep.
+template <int TR, int NW, bool CO = false, bool FUSE = false>
 __device__ __forceinline__ void tile_body(const ScanDesc* d, int lt, unsigned char* smem, int32_t* err) {
   using G = Geo<TR, NW>;
   const Loc L = make_loc(d, lt, TR, G::TC);
@@ -885,17 +952,21 @@ __device__ __forceinline__ void tile_body(const ScanDesc* d, int lt, unsigned ch
   // for range-only input, their elevations' sine and cosine
   long long* rows_s = reinterpret_cast<long long*>(smem + G::off_rows);
   float2* trig_s = reinterpret_cast<float2*>(smem + G::off_trig);
-  for (int k = threadIdx.x; k < L.rn + 3 + RING - 1; k += G::NT) {
-    const int i = L.r0 - 1 + k;
-    long long ro = -1;
-    float2 te = make_float2(0.f, 1.f);
-    if (i >= 0 && i < L.H && k < L.rn + 3) {
-      const int row = ld_in<CO>(d->order + i);
-      if ((unsigned)row < (unsigned)L.H) ro = (long long)row * L.W;
-      if (!d->xyzr) te = ld_in<CO>(d->trig + i);
+  if constexpr (FUSE) {
+    tile_rows_fused<TR, NW>(d, L, lt, smem, err);
+  } else {
+    for (int k = threadIdx.x; k < L.rn + 3 + RING - 1; k += G::NT) {
+      const int i = L.r0 - 1 + k;
+      long long ro = -1;
+      float2 te = make_float2(0.f, 1.f);
+      if (i >= 0 && i < L.H && k < L.rn + 3) {
+        const int row = ld_in<CO>(d->order + i);
+        if ((unsigned)row < (unsigned)L.H) ro = (long long)row * L.W;
+        if (!d->xyzr) te = ld_in<CO>(d->trig + i);
+      }
+      rows_s[k] = ro;
+      if (k < L.rn + 3) trig_s[k] = te;  // trig_s has the sweep's rows only
     }
-    rows_s[k] = ro;
-    if (k < L.rn + 3) trig_s[k] = te;  // trig_s has the sweep's rows only
   }
   __syncthreads();
   const bool angle = d->pred == LSG_PRED_ANGLE;
@@ -911,7 +982,8 @@ __device__ __forceinline__ void tile_body(const ScanDesc* d, int lt, unsigned ch
                           reinterpret_cast<uint32_t*>(smem + G::off_q), d->lroot, d->parent, err);
 }
 
-template <int TR, int NW>
+// FUSE: a single scan launched without k_prep (KArgs::fuse_prep).
+template <int TR, int NW, bool FUSE = false>
 __global__ void __launch_bounds__(NW * 32, 16 / NW) k_tile(const __grid_constant__ KArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   dep_wait();
@@ -919,7 +991,7 @@ __global__ void __launch_bounds__(NW * 32, 16 / NW) k_tile(const __grid_constant
   for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
     int lt;
     const ScanDesc* d = tile_desc(a, t, lt);
-    tile_body<TR, NW>(d, lt, smem, a.err);
+    tile_body<TR, NW, false, FUSE>(d, lt, smem, a.err);
     __syncthreads();
   }
 }
@@ -1542,6 +1614,8 @@ static cudaError_t set_attrs() {
   cudaError_t e = cudaFuncSetAttribute(k_tile<TR, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)Geo<TR, NW>::bytes);
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_tile<TR, NW, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Geo<TR, NW>::bytes);
+  if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_flatten<TR, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)FlatGeo<TR, NW>::bytes);
   if (e != cudaSuccess) return e;
@@ -1612,6 +1686,7 @@ cudaError_t launch_prep(const KArgs& a, cudaStream_t st) {
 
 template <int TR, int NW>
 static cudaError_t run_tile(const KArgs& a, cudaStream_t st, bool pdl) {
+  if (a.fuse_prep) return launch_k(k_tile<TR, NW, true>, a.ntiles, NW * 32, Geo<TR, NW>::bytes, st, pdl, a);
   return launch_k(k_tile<TR, NW>, a.ntiles, NW * 32, Geo<TR, NW>::bytes, st, pdl, a);
 }
 template <int TR, int NW>
