@@ -916,7 +916,9 @@ def main():
             "schedule_ms": sched_ms,
             "roofline": roof,
             "path_roofline": {"bound": "hbm", "achieved": path_achieved, "peak": peak, "unit": "GB/s",
-                              "frac": path_achieved / peak, "bytes_per_point": PATH_BYTES_PER_POINT},
+                              "frac": path_achieved / peak, "bytes_per_point": PATH_BYTES_PER_POINT,
+                              # the aim on large batches: half of the HBM roofline
+                              "target_frac": 0.5, "target_met": path_achieved / peak >= 0.5},
             "kernel_ms": ({"counter_reset": phase[0], "fused": phase[1]} if fused else
                           {"ring_order": phase[0], "tile": phase[1], "merge": phase[2], "labels": phase[3]}),
             "cpu_baseline": cpu,
