@@ -31,6 +31,7 @@ import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -165,14 +166,24 @@ SCHEDULES = {0: "phased (4 launches)", 1: "fused (one persistent launch)",
              2: "grouped (ring order, then 4 scan groups of tile / merge / label launches on parallel graph branches)"}
 
 
+def kernel_code_digest() -> str:
+    """SHA-256 of the kernels' code: lsg_kernels.cu with its comments, trailing
+    blanks and empty lines removed (the file has no comment markers inside
+    string literals), so that editing a comment keeps a capture valid."""
+    src = os.path.join(ROOT, "paper_2005_02704_gb300", "csrc", "lsg_kernels.cu")
+    text = re.sub(r"/\*.*?\*/", "", open(src).read(), flags=re.S)
+    lines = [re.sub(r"//.*$", "", ln).rstrip() for ln in text.splitlines()]
+    return hashlib.sha256("\n".join(ln for ln in lines if ln).encode()).hexdigest()
+
+
 def profiled_values(profile: str):
     """The machine-readable lines (- key: `value`) of a committed ncu summary
-    under profiles/, or None when the kernel source has changed since the
-    capture (the summary's kernel_source_sha256 no longer matches)."""
-    src = os.path.join(ROOT, "paper_2005_02704_gb300", "csrc", "lsg_kernels.cu")
+    under profiles/, or None when the kernels' code has changed since the
+    capture (the summary's kernel_source_sha256, kernel_code_digest() at the
+    time, no longer matches)."""
     prof = os.path.join(ROOT, "profiles", profile)
     try:
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        sha = kernel_code_digest()
         vals = {}
         for line in open(prof):
             if ":" in line and line.strip().startswith("- "):

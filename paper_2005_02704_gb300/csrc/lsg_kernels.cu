@@ -1,8 +1,9 @@
 // lsg_kernels.cu - CUDA kernels (sm_103a) of the Lidar surface-segmentation path.
 //
 // Mukherjee et al., "Fast Geometric Surface based Segmentation of Point Cloud
-// from Lidar Data" (PReMI 2019), Sec. 2 and Algorithm 1.  One pass over a scan
-// (or a batch of scans) is four launches:
+// from Lidar Data" (PReMI 2019), Sec. 2 and Algorithm 1.  One pass over a
+// batch of scans is four launches (a single scan of at most kFuseMaxRings
+// rings: three, its tile kernel doing k_prep's work for the rows it reads):
 //
 //   k_prep     ring order by elevation (rank counting), sin/cos of the sorted
 //              elevations, segment counter reset.               [Sec. 2, point model]
