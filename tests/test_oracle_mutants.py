@@ -45,6 +45,19 @@ MUTANTS = [
     ("back-fill ties to the later column", "if (have_hi && dhi < dlo)", "if (have_hi && dhi <= dlo)"),
     ("back-fill without the other column", "labels[o] = first != -1 ? first : second;", "labels[o] = first;"),
     ("wrap distance off by one", "dhi = W - c;", "dhi = W - c + 1;"),
+    ("rings ordered from the bottom", "while (b >= 0 && (elev[order[b]] < elev[cur] ||",
+     "while (b >= 0 && (elev[order[b]] > elev[cur] ||"),
+    ("ties between rings to the later input row", "(elev[order[b]] == elev[cur] && order[b] > cur))",
+     "(elev[order[b]] == elev[cur] && order[b] < cur))"),
+    ("azimuth of the next column", "double phi = (double)az0 + (double)c * (double)daz;",
+     "double phi = (double)az0 + (double)(c + 1) * (double)daz;"),
+    ("height from the cosine of the elevation", "xyz[3 * dst + 2] = rd * sin(th);",
+     "xyz[3 * dst + 2] = rd * cos(th);"),
+    ("x from the sine of the azimuth", "xyz[3 * dst + 0] = rd * cos(th) * cos(phi);",
+     "xyz[3 * dst + 0] = rd * cos(th) * sin(phi);"),
+    ("diagonal spokes the other way", "static const int dj[6] = {0, +1, +1, 0, -1, -1};",
+     "static const int dj[6] = {0, -1, +1, 0, +1, -1};"),
+    ("spokes not wrapped around the ring", "    if (wr) jj = (jj + Ws) % Ws;\n    if (ii < 0", "    if (ii < 0"),
 ]
 
 
