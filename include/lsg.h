@@ -243,7 +243,8 @@ size_t lsg_memory_used(const lsg_ctx* ctx);
 /*
  * Dynamic batch: one pass over n scans whose set changes from call to call
  * (the serving path).  Same semantics and outputs as n lsg_segment calls, in
- * four launches; the scans' descriptors go to the device through a pinned
+ * four launches (a batch of one: as lsg_segment, three launches when the scan
+ * has at most 256 rings); the scans' descriptors go to the device through a pinned
  * staging buffer of the context (two of them, alternated; a call waits until
  * the copy out of the buffer it reuses has run).  The workspace of all n scans
  * comes from the context, so one context serves one stream at a time.  A
