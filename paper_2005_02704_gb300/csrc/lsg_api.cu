@@ -759,7 +759,7 @@ static cudaError_t capture_io(lsg_plan* pl, cudaStream_t cs, int& launches) {
   std::vector<Copy> elev_all, cnt_all;
   for (int b = 0; b < pl->n; ++b) {
     const ScanDesc& d = pl->host_desc[b];
-    if ((size_t)d.H * d.W)
+    if (d.H > 0 && d.W > 0)
       add_copy(elev_all, const_cast<float*>(pl->dev_in[b].elevation), pl->io[b].elevation, sizeof(float) * d.H);
     add_copy(cnt_all, pl->io[b].nseg, pl->dev_out[b].nseg, sizeof(int32_t));
   }

@@ -5,7 +5,6 @@ import ctypes
 import os
 import re
 
-import pytest
 
 from paper_2005_02704_gb300 import lsg
 

@@ -6,7 +6,6 @@ import ctypes
 import math
 
 import numpy as np
-import pytest
 
 import lidarsim
 from paper_2005_02704_gb300 import lsg

@@ -4,7 +4,6 @@ for timing - is exercised here with two gloo ranks on the CPU."""
 import os
 import socket
 
-import pytest
 import torch
 import torch.distributed as dist
 import torch.multiprocessing as mp
