@@ -5,7 +5,6 @@ import ctypes
 import os
 import re
 
-
 from paper_2005_02704_gb300 import lsg
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
